@@ -1,0 +1,22 @@
+"""Shared test set-up: repo root on sys.path and the ``gpu`` marker."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    """The FP64 CPU oracle (built on first use)."""
+    import oracle
+    oracle.set_threads(int(os.environ.get("ORACLE_THREADS", "0")))
+    return oracle

@@ -1,0 +1,104 @@
+"""Mutation check of the oracle's pins: plant one plausible mistake at a time
+(a dropped term, a wrong sign, factor or index) in a temporary copy of the
+oracle source, rebuild it, and require the pin suite to fail.
+
+Only the temporary copy is changed; the oracle in the tree is untouched.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = [
+    ("F_k last-term sign", "- 0.25 * a * b * c * T", "+ 0.25 * a * b * c * T"),
+    ("F_0 factor", "F[0] = 1.0 - 8.0 * sum;", "F[0] = 1.0 - sum;"),
+    ("f^eq linear term sign", "double term1 = vu / T *", "double term1 = -vu / T *"),
+    ("f^eq linear term factor", "double term1 = vu / T * (1.0 - u2 / (2.0 * T));",
+     "double term1 = vu / T * (1.0 - u2 / (1.0 * T));"),
+    ("f^eq cubic term factor", "(6.0 * T * T * T)", "(2.0 * T * T * T)"),
+    ("f^eq quartic term dropped", "(term0 + term1 + term2 + term3 + term4)",
+     "(term0 + term1 + term2 + term3)"),
+    ("f^eq u^4 factor", "+ u2 * u2 / (8.0 * T * T);", "+ u2 * u2 / (4.0 * T * T);"),
+    ("temperature half dropped", "e += 0.5 * f[q * stride]", "e += f[q * stride]"),
+    ("u_theta moment index", "jt += fq * vth[q];", "jt += fq * vr[q];"),
+    ("M: D T -> T", "(-DIM * T + c2)", "(-T + c2)"),
+    ("M: 2Q/D -> 2Q", "(2.0 * Q / DIM)", "(2.0 * Q)"),
+    ("M: T^2 -> T", "/ (2.0 * T * T) * (2.0 * Q", "/ (2.0 * T) * (2.0 * Q"),
+    ("M dt doubled", "+ M[q] * dt;", "+ M[q] * dt * 2.0;"),
+    ("rate a uses omega2", "aa = p->omega1 * pow(P, p->m);", "aa = p->omega2 * pow(P, p->m);"),
+    ("rate P = rho", "double P = rho * T;", "double P = rho;"),
+    ("ignition gate inverted", "if (T > p->T_th) {", "if (T < p->T_th) {"),
+    ("lambda: printed denominator", "((a + b * lam) * E + b * (1.0 - lam))",
+     "((a + b * lam) * E + a * (1.0 - lam))"),
+    ("lambda: E sign", "double E = exp((a + b) * dt);", "double E = exp(-(a + b) * dt);"),
+    ("streaming sign (both)", "- fr_star - ft_star", "+ fr_star + ft_star"),
+    ("streaming sign (theta)", "- fr_star - ft_star", "- fr_star + ft_star"),
+    ("upwind side swapped (r)", "if (Cr >= 0.0)\n                    fr_star",
+     "if (Cr < 0.0)\n                    fr_star"),
+    ("C_theta without r", "double Ct = vth[q] * dt / (r * dth);", "double Ct = vth[q] * dt / (dth);"),
+    ("C_r scale", "double Cr = vr[q] * dt / dr;", "double Cr = vr[q] * dt / (1.5 * dr);"),
+    ("BGK sign", "(fs[q] - feq[q]) * decay", "(feq[q] - fs[q]) * decay"),
+    ("BGK rate", "const double decay = exp(-dt / p->tau);",
+     "const double decay = exp(-2.0 * dt / p->tau);"),
+    ("lambda advection sign", "lr_star = -ur * (lam[s] - lam[(long)m * p->nr + jm1(j)]) / dr * dt;",
+     "lr_star = ur * (lam[s] - lam[(long)m * p->nr + jm1(j)]) / dr * dt;"),
+    ("lambda theta advection without r",
+     "lt_star = -uth * (lam[s] - lam[(long)mm1(p, m) * p->nr + j]) / (r * dth) * dt;",
+     "lt_star = -uth * (lam[s] - lam[(long)mm1(p, m) * p->nr + j]) / (dth) * dt;"),
+    ("velocity angle sign", "double ang = i * PI / 4.0 - theta;", "double ang = theta - i * PI / 4.0;"),
+    ("v_r and v_theta swapped", "vr[vindex(k, i)] = v[k - 1] * cos(ang);\n            vth[vindex(k, i)] = v[k - 1] * sin(ang);",
+     "vr[vindex(k, i)] = v[k - 1] * sin(ang);\n            vth[vindex(k, i)] = v[k - 1] * cos(ang);"),
+    ("theta wrap", "return m > 0 ? m - 1 : p->ntheta - 1;", "return m > 0 ? m - 1 : 0;"),
+    ("r not cell-centred", "return p->r_in + (j + 0.5) * dr;", "return p->r_in + (j) * dr;"),
+    ("theta grid shifted", "return m * (2.0 * PI / p->ntheta);", "return (m + 0.5) * (2.0 * PI / p->ntheta);"),
+    ("lambda clamp bound", "if (ln > 1.0) { ln = 1.0; ++clamped; }", "if (ln > 0.9) { ln = 0.9; ++clamped; }"),
+    ("outer ghost reflects", "return j < p->nr - 1 ? j + 1 : p->nr - 1;", "return j < p->nr - 1 ? j + 1 : p->nr - 2;"),
+]
+
+PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",
+             "tests/test_oracle_step.py", "tests/test_oracle_cj.py"]
+
+
+def _run_pins(name, old, new):
+    """Run the pin suite on a copy of the oracle with `old` replaced by `new`;
+    returns pytest's summary line."""
+    src = open(os.path.join(ROOT, "oracle", "dbm_oracle.c")).read()
+    assert src.count(old) >= 1, f"mutation pattern not found: {name}"
+    tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
+    try:
+        shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(tmp, "oracle"),
+                        ignore=shutil.ignore_patterns("_build", "__pycache__"))
+        shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                        ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutations.py"))
+        os.makedirs(os.path.join(tmp, "paper_1308_0653_gb300"))
+        for fn in ("__init__.py", "workloads.py"):
+            shutil.copy(os.path.join(ROOT, "paper_1308_0653_gb300", fn),
+                        os.path.join(tmp, "paper_1308_0653_gb300", fn))
+        with open(os.path.join(tmp, "oracle", "dbm_oracle.c"), "w") as fh:
+            fh.write(src.replace(old, new, 1))
+        env = dict(os.environ, ORACLE_THREADS="2")
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                            *PIN_FILES], cwd=tmp, capture_output=True, text=True, timeout=900,
+                           env=env)
+        lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+        return lines[-1] if lines else r.stderr[-200:]
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_fails_a_pin():
+    control = _run_pins("control", "#include <math.h>", "#include <math.h>")
+    assert "passed" in control and "failed" not in control and "error" not in control, control
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        res = dict(zip([m[0] for m in MUTANTS], ex.map(lambda m: _run_pins(*m), MUTANTS)))
+    # caught = a pin assertion failed (a build or collection error does not count)
+    survivors = {k: v for k, v in res.items() if "failed" not in v}
+    assert not survivors, f"mutations not caught by any pin: {survivors}"
