@@ -1,0 +1,363 @@
+"""Benchmark of the fused polar discrete-Boltzmann detonation step on GB300.
+
+A "step" is one time step of the whole update (moments, equilibrium, BGK +
+chemical term, upwind streaming, lambda update) over the 2048 x 2048 reactive
+implosion in FP32 (33 velocities, 1.4e8 site-velocity updates per step; the
+f + lambda state is 0.57 GB per buffer, larger than the 129 MB L2, so no L2
+flush is needed between steps).  The metric is GLUPS = 1e9 site x velocity
+updates per second, with the HBM roofline of the step kernel beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method) on the host cores, on a bounded sample of the same workload.
+Under torchrun every rank runs its own replica (the update is one simulation
+per GPU; no data-path collective), and rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1308_0653_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GLUPS (site x velocity updates/s)"
+UNIT = "GLUPS"
+NV = 33
+BYTES_PER_SITE = {"fp32": 33 * 4 * 2 + 4 * 2, "fp64": 33 * 8 * 2 + 8 * 2}  # f + lambda, read + write
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=64)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nr", type=int, default=2048)
+    ap.add_argument("--ntheta", type=int, default=2048)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+def workload(args):
+    return W.implosion(args.nr, args.ntheta, nsteps=args.steps, seed=0, precision="fp32")
+
+
+def config_of(w, args, extra=None):
+    cfg = {"workload": f"reactive implosion {w.params['nr']}x{w.params['ntheta']} "
+                       "(r in [0.05,1.05], omega1=omega2=2, dt=5e-6, tau=1e-3, seed 0)",
+           "nr": w.params["nr"], "ntheta": w.params["ntheta"], "velocities": NV,
+           "site_velocity_updates_per_step": w.sites * NV,
+           "l2": "inputs larger than L2 (f + lambda state 0.57 GB per buffer vs 129 MB L2); no flush",
+           "parallelism": f"replicas x{args.gpus} (one independent simulation per GPU)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only: the collectives below time the run)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(elapsed_s: float, units: float, backend_device=None):
+    """Max elapsed and summed units over ranks (identity when not distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return elapsed_s, units
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=backend_device)
+    u = torch.tensor([units], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        smax = max(num(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [x for x in sm if x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(num(r[3]) for r in rows)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the oracle
+# ---------------------------------------------------------------------------
+def oracle_sample(w, budget_s=12.0, max_rows=None):
+    """Time the FP64 oracle on the host cores on a bounded sample: whole time
+    steps of the same workload definition (all nr radial sites) on a grid of
+    at most max_rows theta rows, as many steps as fit in budget_s.  The cost
+    per site-velocity update does not depend on the number of rows."""
+    import oracle
+    threads = oracle.set_threads(0)
+    nth = w.params["ntheta"] if max_rows is None else min(max_rows, w.params["ntheta"])
+    sub = W.implosion(w.params["nr"], nth, nsteps=1, seed=0, precision="fp64")
+    p = oracle.make_params(**{k: v for k, v in sub.params.items() if k != "precision"})
+    f, lam = oracle.init(p, sub.fields)
+    t0 = time.perf_counter()
+    f, lam, _ = oracle.step(p, f, lam)
+    one = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    for _ in range(n):
+        f, lam, _ = oracle.step(p, f, lam)
+    el = time.perf_counter() - t0
+    upd = sub.sites * NV * n
+    return {"value": upd / el / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} oracle time steps of the implosion workload definition on a "
+                      f"{w.params['nr']}x{nth} grid (same radial sites, {nth} theta rows "
+                      f"instead of {w.params['ntheta']}), {el:.1f} s on {threads} threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args)
+    # each step: one oracle time step over a row block sized for ~0.05 s
+    import oracle
+    threads = oracle.set_threads(0)
+    probe = oracle_sample(w, budget_s=1.0, max_rows=64)
+    rate = probe["value"] * 1e9  # updates/s
+    rows = int(max(8, min(w.params["ntheta"], 0.05 * rate / (w.params["nr"] * NV))))
+    sub = W.implosion(w.params["nr"], rows, nsteps=1, seed=0, precision="fp64")
+    p = oracle.make_params(**{k: v for k, v in sub.params.items() if k != "precision"})
+    f, lam = oracle.init(p, sub.fields)
+    for _ in range(args.warmup):
+        f, lam, _ = oracle.step(p, f, lam)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, lam, _ = oracle.step(p, f, lam)
+    el = time.perf_counter() - t0
+    upd = sub.sites * NV * args.steps
+    value = upd / el / 1e9
+    sample = (f"each step: one oracle time step of the implosion workload definition on a "
+              f"{w.params['nr']}x{rows} grid (same radial sites, {rows} theta rows instead of "
+              f"{w.params['ntheta']}), {threads} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w, args, {"reference_rows_per_step": rows}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU side
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1308_0653_gb300 import dbm
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = workload(args)
+    sites = w.sites
+    stream = torch.cuda.Stream(device=dev)
+
+    sim = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
+    sim.init_state(w.fields, stream=stream)
+    sim.step(args.warmup, stream=stream)
+    torch.cuda.synchronize(dev)
+
+    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    clocks = ClockSampler(vis[local] if local < len(vis) else str(local))
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    mom = sim.moments(stream=stream, raise_nonfinite=False)
+    finite = mom["status"] == dbm.DBM_OK
+    launch = sim.launch_info()
+    elapsed_max, units = aggregate(elapsed, float(sites) * NV * args.steps,
+                                   backend_device=dev if ws > 1 else None)
+    value = units / elapsed_max / 1e9
+
+    # roofline of the step kernel (the only kernel in the timed region)
+    per_launch = elapsed / args.steps
+    alg_bytes = BYTES_PER_SITE["fp32"] * sites
+    achieved = alg_bytes / per_launch / 1e9
+    peak, peak_src = measured_peak()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "dbm::step_kernel<float,128,6>",
+            "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch * 1e3,
+            "peak_source": peak_src}
+    sim.close()
+
+    # FP64 path on the same workload (ALU-bound on GB300), for the FP32 vs FP64 ratio
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = dbm.Simulation(dict(w.params, precision="fp64"), device=dev)
+        s64.init_state(w.fields, stream=stream)
+        s64.step(4, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        s64.step(args.fp64_steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        el64 = e0.elapsed_time(e1) / 1e3
+        fp64 = {"value": sites * NV * args.fp64_steps / el64 / 1e9, "unit": UNIT,
+                "steps": args.fp64_steps, "kernel": "dbm::step_kernel<double,64,5>"}
+        s64.close()
+
+    # end to end through the C ABI with pinned host buffers: init from host,
+    # K time steps, moments back to host (one solve; copies inside the timing)
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: torch.from_numpy(w.fields[k]).pin_memory() for k in dbm.FIELDS}
+        host_in = {k: v.numpy() for k, v in pinned.items()}
+        outs = {k: torch.empty(w.fields[k].shape, dtype=torch.float64).pin_memory().numpy()
+                for k in dbm.FIELDS}
+        tot = np.zeros(4)
+        sim = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
+        sim.init_state(host_in, stream=stream)  # warm the path once
+        sim.step(GRAPH_WARM, stream=stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        dbm.dbm_init_state(sim.h, *[host_in[k] for k in dbm.FIELDS], stream=stream)
+        dbm.dbm_step(sim.h, args.steps, stream)
+        dbm.dbm_moments(sim.h, *[outs[k] for k in dbm.FIELDS], totals=tot, stream=stream)
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        sim.close()
+        t_e2e_max, units_e2e = aggregate(t_e2e, float(sites) * NV * args.steps,
+                                         backend_device=dev if ws > 1 else None)
+        h2d = 5 * sites * 8
+        d2h = 5 * sites * 8 + 4 * 8 + 4
+        e2e = {"value": units_e2e / t_e2e_max / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "solve": {"time_steps": args.steps, "h2d_bytes": h2d, "d2h_bytes": d2h,
+                         "seconds": t_e2e,
+                         "calls": "dbm_init_state(host) + dbm_step(K) + dbm_moments(host)"}}
+
+    cpu = None
+    if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(w, budget_s=12.0, max_rows=256)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(w, args, {"launch": launch}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": args.steps, "fp64": fp64,
+                "fp32_over_fp64": (value / args.gpus / fp64["value"]) if fp64 else None,
+                "state_finite": bool(finite)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+GRAPH_WARM = 64
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

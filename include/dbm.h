@@ -1,0 +1,193 @@
+/*
+ * dbm.h - C ABI of the GB300 (sm_103a) polar-coordinate discrete-Boltzmann
+ * detonation update of Lin, Xu, Zhang and Li, "Polar coordinate lattice
+ * Boltzmann kinetic modeling of detonation phenomena" (arXiv:1308.0653).
+ *
+ * One time step advances every grid site (i_r, i_theta) and each of the 33
+ * discrete velocities of the D2V33 set (Sec. II.B): moments -> equilibrium
+ * f^eq (Eq. feq) -> BGK relaxation integrated exactly + chemical term M
+ * (Eq. LB_evolution_equation, Sec. II.B) -> first-order upwind streaming in r
+ * and theta -> reaction progress lambda by the exact solution of Cochran's
+ * rate law plus upwind transport (Eq. Cochran, Eq. Eqlambda).
+ *
+ * Conventions shared by every entry point:
+ *   grid      r_j = r_in + (j + 1/2) dr, dr = (r_out - r_in) / nr, j = 0..nr-1;
+ *             theta_m = m dtheta, dtheta = 2 pi / ntheta, m = 0..ntheta-1.
+ *   fields    host or device arrays of double, row-major [ntheta][nr]
+ *             (index m * nr + j); velocities in polar components u_r, u_theta.
+ *   velocity  index v = 0 for the rest particle, v = 1 + 8 (k - 1) + i for
+ *             speed v_k (k = 1..4) in Cartesian direction i pi / 4 (i = 0..7).
+ *   streams   `stream` arguments are cudaStream_t values passed as void*;
+ *             NULL means the legacy default stream.
+ *   status    every function returns a DBM_* status and never aborts or
+ *             exits; dbm_strerror() names it.  Errors raised by work already
+ *             queued on the GPU surface at the next call that synchronises
+ *             (dbm_moments, dbm_status, dbm_poll).
+ *   memory    device memory is supplied by the caller (for example a PyTorch
+ *             tensor) and only borrowed by the library until the matching
+ *             destroy call; host arrays are caller-owned and only read or
+ *             written during the call (or, for dbm_submit, copied).
+ *
+ * Readings of the paper taken where it is garbled or silent (all documented
+ * in the library's design notes): the last term of F_k has a minus sign; the
+ * lambda-update denominator is (a + b lam) E + b (1 - lam); the streaming
+ * terms are subtracted (upwind); radial boundaries are zero-gradient ghosts;
+ * f starts at f^eq of the initial fields; lambda is kept in [0, 1].
+ */
+#ifndef DBM_H
+#define DBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define DBM_OK          0  /* success                                              */
+#define DBM_EINVAL      1  /* invalid argument (NULL pointer, size, parameter)     */
+#define DBM_ECFL        2  /* max |C_r| + |C_theta| > 1: first-order upwind unstable */
+#define DBM_ENOMEM      3  /* caller buffer too small / server pool exhausted      */
+#define DBM_EBUSY       4  /* server queue full                                    */
+#define DBM_ENOTREADY   5  /* request still queued or running                      */
+#define DBM_ETIMEOUT    6  /* a bounded wait (host or device) gave up              */
+#define DBM_ENONFINITE  7  /* a moment came out NaN or infinite                    */
+#define DBM_ECUDA       8  /* a CUDA runtime call failed                           */
+#define DBM_ECANCELLED  9  /* request cancelled before it finished                 */
+#define DBM_ENOTFOUND  10  /* unknown ticket                                       */
+
+#define DBM_NV 33          /* D2V33: 1 rest + 4 rings x 8 directions (Sec. II.B)  */
+
+/* precision of f and of the per-step arithmetic */
+#define DBM_FP32 0
+#define DBM_FP64 1
+
+/* radial boundary rule (Sec. II.D defers it to an earlier paper; reading) */
+#define DBM_BC_OUTFLOW 0   /* zero-gradient ghost: f(-1) = f(0), f(nr) = f(nr-1) */
+
+/* heat put into f by M (Sec. II.B) */
+#define DBM_R_EXPLICIT   0 /* R(lambda^t, P^t) of Eq. (Cochran): the paper's form */
+#define DBM_R_CONSISTENT 1 /* R = (lambda_react - lambda^t) / dt: heat = rho Q dlam */
+
+/* ---- parameters of one simulation --------------------------------------- */
+typedef struct dbm_params {
+    int32_t nr, ntheta;        /* grid size, both >= 1                            */
+    int32_t precision;         /* DBM_FP32 or DBM_FP64                            */
+    int32_t reaction_energy;   /* DBM_R_EXPLICIT (default) or DBM_R_CONSISTENT     */
+    int32_t r_bc_inner;        /* DBM_BC_OUTFLOW                                  */
+    int32_t r_bc_outer;        /* DBM_BC_OUTFLOW                                  */
+    int32_t rows_per_item;     /* theta rows per CTA work item; 0 = automatic     */
+    int32_t reserved;          /* must be 0                                       */
+    double r_in, r_out;        /* annulus radii, 0 < r_in < r_out (Sec. II.D)     */
+    double dt, tau;            /* time step and BGK relaxation time (Sec. II.C)   */
+    double Q;                  /* heat release per unit mass (Sec. II.A)          */
+    double omega1, omega2;     /* Cochran rate constants, >= 0 (Eq. Cochran)      */
+    double m, n;               /* Cochran pressure exponents (paper: 1, 1)        */
+    double T_th;               /* ignition temperature (paper: 1.1)               */
+    double v[4];               /* ring speeds v_1..v_4 (paper: 1.5 3.5 7.5 12.5)  */
+} dbm_params;
+
+typedef struct dbm_s dbm_t;    /* one simulation bound to a caller device buffer */
+
+/* Library version string (static storage). */
+const char *dbm_version(void);
+
+/* Static text naming a status code. */
+const char *dbm_strerror(int status);
+
+/* Text of the last CUDA failure reported as DBM_ECUDA on this thread
+ * (thread-local static storage; empty if none). */
+const char *dbm_last_error(void);
+
+/* Fill *p with the paper's constants (Sec. II.B, III.A) and a 64 x 64 annulus
+ * r in [0.05, 1.05], dt 1e-5, tau 1e-3, Q 1, omega1 = omega2 = 0, FP32. */
+int dbm_params_default(dbm_params *p);
+
+/* Host-only validation of *p (no GPU needed).  Checks sizes, radii, dt, tau,
+ * rate constants and the Courant condition of Sec. II.C,
+ *   max over velocities, rows and radii of |C_r| + |C_theta| <= 1,
+ *   C_r = v_kir dt / dr, C_theta = v_kith dt / (r dtheta);
+ * writes that maximum to *cfl when cfl is not NULL.
+ * Returns DBM_OK, DBM_EINVAL or DBM_ECFL. */
+int dbm_check(const dbm_params *p, double *cfl);
+
+/* Host-only: bytes of caller device memory dbm_create needs for *p (two f
+ * buffers, two lambda buffers, geometry tables, status and reduction words),
+ * or 0 if *p is invalid. */
+size_t dbm_state_bytes(const dbm_params *p);
+
+/* Bind a simulation to caller device memory dev_buf (dev_bytes >=
+ * dbm_state_bytes(p), 256-byte aligned, on the current device).  Uploads the
+ * geometry tables and clears the buffer (synchronous).  The caller keeps
+ * ownership of dev_buf and must keep it alive until dbm_destroy.
+ * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (buffer too small), DBM_ECUDA. */
+int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out);
+
+/* Release the handle (not dev_buf).  Waits for no GPU work: the caller must
+ * not destroy a handle whose work is still queued. */
+int dbm_destroy(dbm_t *h);
+
+/* Set the state at t = 0 from host fields rho, u_r, u_theta, T, lambda
+ * ([ntheta][nr] doubles each, caller-owned, read during the call): f = f^eq
+ * of the fields at every site, lambda copied (reading: the paper gives
+ * macroscopic initial data only).  Enqueued on `stream`; the host arrays are
+ * copied before the call returns.  Resets the step counter.
+ * Errors: DBM_EINVAL (NULL array, rho <= 0 or T <= 0 or non-finite value),
+ * DBM_ECUDA. */
+int dbm_init_state(dbm_t *h, const double *rho, const double *ur, const double *uth,
+                   const double *T, const double *lam, void *stream);
+
+/* As dbm_init_state with device-resident fields: d_fields points to
+ * 5 * ntheta * nr doubles laid out [field][ntheta][nr] in the order rho, u_r,
+ * u_theta, T, lambda (read by the GPU in stream order). */
+int dbm_init_state_device(dbm_t *h, const double *d_fields, void *stream);
+
+/* Enqueue nsteps time steps (Eq. LB_evolution_equation + Eq. Eqlambda) on
+ * `stream`; asynchronous.  nsteps = 0 is a no-op.  Uses a CUDA graph of the
+ * step kernel for long runs.  Errors: DBM_EINVAL (nsteps < 0), DBM_ECUDA. */
+int dbm_step(dbm_t *h, int64_t nsteps, void *stream);
+
+/* Macroscopic fields of the current state, copied to host arrays (any may be
+ * NULL): rho = sum f, u = sum f v / rho in polar components, T = sum f
+ * (v - u)^2 / (2 rho) (Sec. II.B), lambda.  Moments are evaluated in FP64
+ * from f.  totals (may be NULL) receives the FP64 area-weighted sums
+ * {mass, momentum_x, momentum_y, energy}, energy = rho T + rho u^2 / 2,
+ * weight r dr dtheta.  Synchronises `stream`.
+ * Errors: DBM_ENONFINITE (some moment is NaN/inf; outputs still written),
+ * DBM_ETIMEOUT (a step kernel's bounded wait expired), DBM_ECUDA. */
+int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, double *lam,
+                double totals[4], void *stream);
+
+/* As dbm_moments into device memory d_out (5 * ntheta * nr doubles,
+ * [field][ntheta][nr], order rho, u_r, u_theta, T, lambda); asynchronous, no
+ * totals, no status check. */
+int dbm_moments_device(dbm_t *h, double *d_out, void *stream);
+
+/* Steps taken since the last init or import. */
+int64_t dbm_steps_done(const dbm_t *h);
+
+/* Synchronise `stream` and report the sticky device status word: DBM_OK,
+ * DBM_ETIMEOUT (a bounded wait in a step kernel expired) or DBM_ECUDA. */
+int dbm_status(dbm_t *h, void *stream);
+
+/* Checkpoint: copy the raw state to host memory.  f receives 33 * ntheta * nr
+ * values and lam ntheta * nr values in the handle's precision (float for
+ * DBM_FP32, double for DBM_FP64), layout f[v][ntheta][nr]; *steps receives the
+ * step counter.  Synchronises `stream`. */
+int dbm_export_state(dbm_t *h, void *f, void *lam, int64_t *steps, void *stream);
+
+/* Restore a state written by dbm_export_state (same layout and precision);
+ * resuming is bitwise identical to an uninterrupted run.  Synchronises. */
+int dbm_import_state(dbm_t *h, const void *f, const void *lam, int64_t steps, void *stream);
+
+/* Launch shape chosen at create time (any pointer may be NULL): persistent
+ * CTAs in the grid, threads (radial sites) per CTA, dynamic shared memory per
+ * CTA, theta rows per work item and the number of work items per step. */
+int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes,
+                    int *rows_per_item, int *items);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBM_H */

@@ -1,0 +1,591 @@
+// Device code of the polar-coordinate discrete-Boltzmann detonation update
+// (Lin, Xu, Zhang, Li, arXiv:1308.0653) for sm_103a.
+//
+// Data layout in HBM (one instance):
+//   f[v][theta][ld]   33 planes, row length ld = nr rounded up to 32 elements,
+//                     r contiguous (coalesced 128-byte rows)
+//   lam[theta][ld]    reaction progress lambda
+//   rowtab[theta][16] cos(i pi/4 - theta_m), sin(i pi/4 - theta_m), i = 0..7
+//   inv_r[ld]         1 / r_j at cell centres
+//
+// The fused step kernel is persistent: each CTA owns W consecutive radial
+// sites (one per thread) of a run of theta rows ("work item") and marches down
+// the rows.  A ring of NSTAGE shared-memory row buffers, each holding all 33
+// f planes plus lambda for the strip and a 16-byte halo on both radial sides,
+// is filled by TMA bulk copies (cp.async.bulk, completion on an mbarrier per
+// buffer).  Row m is computed from buffers m-1, m, m+1, so every f value is
+// read from HBM once per step (plus the halo columns and two halo rows per
+// item) and written once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dbm {
+
+constexpr int NV = 33;    // D2V33 velocities (Sec. II.B)
+constexpr int NARR = 34;  // 33 f planes + lambda
+
+// Status bits written by kernels into the instance's status word.
+constexpr int ST_WAIT_TIMEOUT = 1;   // an mbarrier wait gave up
+constexpr int ST_NONFINITE = 2;      // a moment was NaN / inf (moments kernel)
+
+template <typename real> struct Halo;
+template <> struct Halo<float> { static constexpr int value = 4; };   // 16 bytes
+template <> struct Halo<double> { static constexpr int value = 2; };  // 16 bytes
+
+// Per-instance constants of the step (host-computed in double, rounded to real).
+template <typename real>
+struct StepArgs {
+    const real *f_in;
+    real *f_out;
+    const real *lam_in;
+    real *lam_out;
+    const real *rowtab;   // [ntheta][16]
+    const real *inv_r;    // [ld]
+    int *status;          // sticky status word
+    long long plane;      // ntheta * ld (elements between f planes)
+    int nr, ntheta, ld;
+    int strips;           // ceil(nr / W)
+    int rows_per_item;    // theta rows per work item
+    int segs;             // ceil(ntheta / rows_per_item)
+    int items;            // strips * segs
+    int reaction_energy;  // 0 explicit R, 1 consistent R
+    int general_pow;      // 0: m = n = 1 (P^m = P), 1: pow()
+    real cr_scale;        // dt / dr
+    real ct_scale;        // dt / dtheta
+    real decay;           // exp(-dt / tau)
+    real one_m_decay;     // 1 - exp(-dt / tau)
+    real dt, Q, omega1, omega2, m_exp, n_exp, T_th;
+    real v[4], v2[4];     // ring speeds and their squares
+    real Fc[4][4];        // F_k(T) = T (Fc[k][0] + T (Fc[k][1] + T (Fc[k][2] + T Fc[k][3])))
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers (mbarrier + TMA bulk copy)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM cycles (about a second) and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <typename real> __device__ __forceinline__ real rcp_(real x) { return real(1) / x; }
+
+template <typename real> __device__ __forceinline__ real expm1_(real x);
+template <> __device__ __forceinline__ float expm1_<float>(float x) { return expm1f(x); }
+template <> __device__ __forceinline__ double expm1_<double>(double x) { return expm1(x); }
+
+template <typename real> __device__ __forceinline__ real pow_(real x, real y);
+template <> __device__ __forceinline__ float pow_<float>(float x, float y) { return powf(x, y); }
+template <> __device__ __forceinline__ double pow_<double>(double x, double y) { return pow(x, y); }
+
+// ---------------------------------------------------------------------------
+// Work-item decoding: item -> (strip j0, rows [mb, me))
+// ---------------------------------------------------------------------------
+template <typename real, int W>
+__device__ __forceinline__ void decode_item(const StepArgs<real> &A, int item, int &j0, int &mb,
+                                            int &me)
+{
+    const int strip = item % A.strips;
+    const int seg = item / A.strips;
+    j0 = strip * W;
+    mb = seg * A.rows_per_item;
+    me = min(mb + A.rows_per_item, A.ntheta);
+}
+
+// ---------------------------------------------------------------------------
+// One site's update (Eq. LB_evolution_equation, Eq. Eqlambda), all 33
+// velocities unrolled.  sp/sc/sn: shared-memory buffers of rows m-1, m, m+1;
+// col = HALO + tx.  Velocity (k, i) has Cartesian direction i pi / 4, so its
+// moments and equilibrium use the fixed direction cosines; its polar Courant
+// numbers use the row's c_i = cos(i pi/4 - theta_m), s_i = sin(...).
+// ---------------------------------------------------------------------------
+template <typename real, int WP>
+__device__ __forceinline__ void site_update(const StepArgs<real> &A, const real *__restrict__ sp,
+                                            const real *__restrict__ sc,
+                                            const real *__restrict__ sn, int col, int j, int m,
+                                            real inv_r, const real (&cs)[8], const real (&sn8)[8])
+{
+    const real H = real(0.70710678118654752440);  // cos(pi/4)
+
+    // --- a1: load the site's 33 f and lambda -------------------------------
+    real f[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) f[q] = sc[q * WP + col];
+    const real lam = sc[NV * WP + col];
+
+    // --- a2: moments, ring by ring (Cartesian components) ------------------
+    real rho = f[0], jx = real(0), jy = real(0), e2 = real(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const real *g = &f[1 + 8 * k];
+        const real s0 = ((g[0] + g[4]) + (g[2] + g[6])) + ((g[1] + g[5]) + (g[3] + g[7]));
+        const real a = g[1] - g[5], b = g[3] - g[7];
+        const real sx = (g[0] - g[4]) + H * (a - b);
+        const real sy = (g[2] - g[6]) + H * (a + b);
+        rho += s0;
+        jx += A.v[k] * sx;
+        jy += A.v[k] * sy;
+        e2 += A.v2[k] * s0;
+    }
+    const real inv_rho = rcp_(rho);
+    const real ux = jx * inv_rho, uy = jy * inv_rho;
+    const real u2 = ux * ux + uy * uy;
+    const real T = real(0.5) * (e2 * inv_rho - u2);
+    const real inv_T = rcp_(T);
+
+    // --- a3: weights F_k(T), F_0 = 1 - 8 sum F_k ---------------------------
+    real F[4];
+    real Fsum = real(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        F[k] = T * (A.Fc[k][0] + T * (A.Fc[k][1] + T * (A.Fc[k][2] + T * A.Fc[k][3])));
+        Fsum += F[k];
+    }
+    const real F0 = real(1) - real(8) * Fsum;
+
+    // --- a4 coefficients: f^eq = rho F_k [A0 + A1 xi + A2 xi^2 + xi^3/6 + xi^4/24],
+    //     xi = v.u / T ---------------------------------------------------------
+    const real hh = real(0.5) * u2 * inv_T;
+    const real A0 = real(1) - hh + real(0.5) * hh * hh;
+    const real A1 = real(1) - hh;
+    const real A2 = real(0.5) * A1;
+    const real wx = ux * inv_T, wy = uy * inv_T;
+    real w[8];
+    w[0] = wx;
+    w[2] = wy;
+    w[1] = H * (wx + wy);
+    w[3] = H * (wy - wx);
+    w[4] = -w[0];
+    w[5] = -w[1];
+    w[6] = -w[2];
+    w[7] = -w[3];
+
+    // --- a5: Cochran rate with ignition gate; exact lambda step (a9) -------
+    const real P = rho * T;
+    real a = real(0), b = real(0);
+    if (T > A.T_th) {
+        if (A.general_pow) {
+            a = A.omega1 * pow_(P, A.m_exp);
+            b = A.omega2 * pow_(P, A.n_exp);
+        } else {
+            a = A.omega1 * P;
+            b = A.omega2 * P;
+        }
+    }
+    const real om = real(1) - lam;
+    const real g = a + b * lam;
+    real R = om * g;
+    const real sab = a + b;
+    real dlam = real(0);
+    if (sab > real(0)) {
+        const real em1 = expm1_(sab * A.dt);
+        dlam = om * g * em1 / (sab + g * em1);
+    }
+    if (A.reaction_energy) R = dlam / A.dt;
+
+    // --- a6+a7 coefficients: f_new = poly(xi) (beta_k - gamma_k xi) + ... ---
+    //     M = f^eq ((v-u)^2 - 2T) / (2T^2) Q R with (v-u)^2 = v_k^2 + u^2 - 2 T xi
+    const real QR = A.Q * R;
+    const real half_inv_T2 = real(0.5) * inv_T * inv_T;
+    const real gam = A.dt * QR * inv_T;
+    const real beta0 = rho * F0 * (A.one_m_decay + A.dt * QR * (u2 - real(2) * T) * half_inv_T2);
+
+    // --- a8: per-direction Courant magnitudes and upwind neighbours --------
+    real ar[8], at[8], sa[8];
+    int rn[8], tn[8];
+    const int to_prev = (int)(sp - sc), to_next = (int)(sn - sc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        ar[i] = fabs(cs[i]) * A.cr_scale;
+        at[i] = fabs(sn8[i]) * A.ct_scale * inv_r;
+        sa[i] = ar[i] + at[i];
+        int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
+        if ((j == 0 && o < 0) || (j == A.nr - 1 && o > 0)) o = 0;  // zero-gradient ghost
+        rn[i] = col + o;
+        tn[i] = col + (sn8[i] >= real(0) ? to_prev : to_next);  // C_theta >= 0: row m-1
+    }
+
+    // --- a7 + a11: update all velocities and store ------------------------
+    real *out = A.f_out + (long long)m * A.ld + j;
+    out[0] = A0 * beta0 + A.decay * f[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const real vk = A.v[k];
+        const real rF = rho * F[k];
+        const real beta = rF * (A.one_m_decay + A.dt * QR * (A.v2[k] + u2 - real(2) * T) * half_inv_T2);
+        const real gamma = rF * gam;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int q = 1 + 8 * k + i;
+            const real xi = vk * w[i];
+            const real poly = A0 + xi * (A1 + xi * (A2 + xi * (real(1.0 / 6.0) + xi * real(1.0 / 24.0))));
+            real t = poly * (beta - gamma * xi);
+            t += (A.decay - vk * sa[i]) * f[q];
+            const real adv = ar[i] * sc[q * WP + rn[i]] + at[i] * sc[q * WP + tn[i]];
+            t += vk * adv;
+            out[(long long)q * A.plane] = t;
+        }
+    }
+
+    // --- a9 + a10: lambda = exact reaction step + upwind transport ---------
+    const real cth = cs[0], sth = -sn8[0];  // cos(theta_m), sin(theta_m)
+    const real ur = ux * cth + uy * sth;
+    const real uth = -ux * sth + uy * cth;
+    int orr = ur >= real(0) ? -1 : 1;
+    if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
+    const real lr = sc[NV * WP + col + orr];
+    const real lt = (uth >= real(0) ? sp : sn)[NV * WP + col];
+    real ln = lam + dlam - fabs(ur) * A.cr_scale * (lam - lr) -
+              fabs(uth) * A.ct_scale * inv_r * (lam - lt);
+    ln = fmin(fmax(ln, real(0)), real(1));
+    A.lam_out[(long long)m * A.ld + j] = ln;
+}
+
+// ---------------------------------------------------------------------------
+// The fused persistent step kernel.
+// ---------------------------------------------------------------------------
+template <typename real, int W, int NSTAGE>
+__global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ StepArgs<real> A)
+{
+    constexpr int HALO = Halo<real>::value;
+    constexpr int WP = W + 2 * HALO;
+    constexpr int SLOT = NARR * WP;  // elements per row buffer
+    static_assert(NSTAGE >= 3, "rows m-1, m, m+1 must be resident");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    real *sm = reinterpret_cast<real *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + sizeof(real) * NSTAGE * SLOT);
+    __shared__ int abort_flag;
+
+    const int tx = threadIdx.x;
+    const int lane = tx & 31;
+    const bool producer = tx < 32;  // warp 0 issues the copies
+
+    if (tx == 0) {
+        for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    // Total row loads of this CTA: rows mb-1 .. me for each of its items.
+    long long total_loads = 0;
+    for (int it = blockIdx.x; it < A.items; it += gridDim.x) {
+        int j0, mb, me;
+        decode_item<real, W>(A, it, j0, mb, me);
+        total_loads += (me - mb) + 2;
+    }
+
+    // Producer cursor (replicated in the lanes of warp 0).
+    long long issued = 0;
+    int p_item = blockIdx.x, p_row = 0;
+
+    auto issue_one = [&]() {
+        int j0, mb, me;
+        decode_item<real, W>(A, p_item, j0, mb, me);
+        int m = mb - 1 + p_row;
+        m = m < 0 ? m + A.ntheta : (m >= A.ntheta ? m - A.ntheta : m);
+        const int slot = (int)(issued % NSTAGE);
+        const int jlo = max(j0 - HALO, 0);
+        const int jhi = min(j0 + W + HALO, A.ld);
+        const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
+        real *dst = sm + slot * SLOT + (jlo - (j0 - HALO));
+        if (lane == 0) mbar_arrive_expect_tx(&bars[slot], nbytes * NARR);
+        __syncwarp();
+        for (int a = lane; a < NARR; a += 32) {
+            const real *src = (a < NV) ? A.f_in + (long long)a * A.plane + (long long)m * A.ld + jlo
+                                       : A.lam_in + (long long)m * A.ld + jlo;
+            bulk_g2s(dst + a * WP, src, nbytes, &bars[slot]);
+        }
+        ++issued;
+        if (++p_row == (me - mb) + 2) {
+            p_row = 0;
+            p_item += gridDim.x;
+        }
+    };
+
+    if (producer) {
+        while (issued < NSTAGE && issued < total_loads) issue_one();
+    }
+
+    long long base = 0;  // sequence position of the current item's first load
+    bool ok = true;
+    for (int it = blockIdx.x; it < A.items && ok; it += gridDim.x) {
+        int j0, mb, me;
+        decode_item<real, W>(A, it, j0, mb, me);
+        const int L = me - mb;
+        const int j = j0 + tx;
+        const bool active = j < A.nr;
+        const real inv_r = A.inv_r[active ? j : 0];
+
+        for (int c = 1; c <= L; ++c) {
+            const long long P = base + c;
+            // wait for rows at positions P-1, P, P+1
+#pragma unroll
+            for (int d = -1; d <= 1; ++d) {
+                const long long Q = P + d;
+                if (!mbar_wait_bounded(&bars[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1))) {
+                    atomicOr(A.status, ST_WAIT_TIMEOUT);
+                    abort_flag = 1;
+                }
+            }
+            const int m = mb + c - 1;
+            if (active && !abort_flag) {
+                real cs[8], sn8[8];
+                const real *rt = A.rowtab + (long long)m * 16;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    cs[i] = rt[i];
+                    sn8[i] = rt[8 + i];
+                }
+                site_update<real, WP>(A, sm + ((P - 1) % NSTAGE) * SLOT, sm + (P % NSTAGE) * SLOT,
+                                      sm + ((P + 1) % NSTAGE) * SLOT, HALO + tx, j, m, inv_r, cs, sn8);
+            }
+            __syncthreads();
+            if (abort_flag) {
+                ok = false;
+                break;
+            }
+            // positions before need_from are no longer read
+            const long long need_from = (c < L) ? P : base + L + 2;
+            if (producer) {
+                fence_proxy_async_smem();
+                while (issued < need_from + NSTAGE && issued < total_loads) issue_one();
+            }
+        }
+        base += L + 2;
+    }
+
+    if (!ok && tx == 0) {
+        // Drain: wait (bounded) for every copy still in flight before exiting.
+        for (long long Q = base; Q < issued; ++Q) mbar_wait_bounded(&bars[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: f = f^eq(rho, u, T) (Eq. feq) in FP64, rounded once to real.
+// fields: [5][ntheta][nr] doubles (rho, u_r, u_theta, T, lambda).
+// ---------------------------------------------------------------------------
+template <typename real>
+struct InitArgs {
+    const double *fields;
+    real *f;
+    real *lam;
+    long long plane;
+    int nr, ntheta, ld;
+    double v[4];
+    double Fc[4][4];
+};
+
+__device__ __forceinline__ void cart_dirs(double (&cx)[8], double (&cy)[8])
+{
+    const double H = 0.70710678118654752440;
+    const double c[8] = {1.0, H, 0.0, -H, -1.0, -H, 0.0, H};
+    const double sn[8] = {0.0, H, 1.0, H, 0.0, -H, -1.0, -H};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        cx[i] = c[i];
+        cy[i] = sn[i];
+    }
+}
+
+template <typename real>
+__global__ void init_kernel(const InitArgs<real> A)
+{
+    const long long N = (long long)A.nr * A.ntheta;
+    double cx[8], cy[8];
+    cart_dirs(cx, cy);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
+        const double rho = A.fields[s], ur = A.fields[N + s], uth = A.fields[2 * N + s];
+        const double T = A.fields[3 * N + s], lam = A.fields[4 * N + s];
+        double sth, cth;
+        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        const double ux = ur * cth - uth * sth, uy = ur * sth + uth * cth;
+        const double u2 = ux * ux + uy * uy;
+        double F[4], Fsum = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            F[k] = T * (A.Fc[k][0] + T * (A.Fc[k][1] + T * (A.Fc[k][2] + T * A.Fc[k][3])));
+            Fsum += F[k];
+        }
+        const double F0 = 1.0 - 8.0 * Fsum;
+        const double hh = 0.5 * u2 / T;
+        const double A0 = 1.0 - hh + 0.5 * hh * hh, A1 = 1.0 - hh, A2 = 0.5 * A1;
+        real *out = A.f + (long long)m * A.ld + j;
+        out[0] = (real)(rho * F0 * A0);
+        for (int k = 0; k < 4; ++k) {
+            for (int i = 0; i < 8; ++i) {
+                const double xi = A.v[k] * (cx[i] * ux + cy[i] * uy) / T;
+                const double poly = A0 + xi * (A1 + xi * (A2 + xi * (1.0 / 6.0 + xi * (1.0 / 24.0))));
+                out[(long long)(1 + 8 * k + i) * A.plane] = (real)(rho * F[k] * poly);
+            }
+        }
+        A.lam[(long long)m * A.ld + j] = (real)lam;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Moments (Sec. II.B) in FP64 from f, plus per-block partial sums of the
+// area-weighted totals {mass, momentum x, momentum y, energy}.
+// out: [5][ntheta][nr] doubles; partials: [gridDim.x][4] (scratch).
+// ---------------------------------------------------------------------------
+template <typename real>
+struct MomArgs {
+    const real *f;
+    const real *lam;
+    double *out;
+    double *partials;
+    int *status;
+    long long plane;
+    int nr, ntheta, ld;
+    double r_in, dr, dtheta;
+    double v[4];
+};
+
+template <typename real>
+__global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
+{
+    const long long N = (long long)A.nr * A.ntheta;
+    double cx[8], cy[8];
+    cart_dirs(cx, cy);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    bool bad = false;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
+        const real *fp = A.f + (long long)m * A.ld + j;
+        double fv[NV];
+        for (int q = 0; q < NV; ++q) fv[q] = (double)fp[(long long)q * A.plane];
+        double rho = fv[0], jx = 0.0, jy = 0.0;
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < 8; ++i) {
+                const double fq = fv[1 + 8 * k + i];
+                rho += fq;
+                jx += fq * A.v[k] * cx[i];
+                jy += fq * A.v[k] * cy[i];
+            }
+        const double ux = jx / rho, uy = jy / rho;
+        double e = 0.5 * fv[0] * (ux * ux + uy * uy);
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < 8; ++i) {
+                const double dx = A.v[k] * cx[i] - ux, dy = A.v[k] * cy[i] - uy;
+                e += 0.5 * fv[1 + 8 * k + i] * (dx * dx + dy * dy);
+            }
+        const double T = e / rho;
+        double sth, cth;
+        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        const double ur = ux * cth + uy * sth, uth = -ux * sth + uy * cth;
+        const double lam = (double)A.lam[(long long)m * A.ld + j];
+        if (A.out) {
+            A.out[s] = rho;
+            A.out[N + s] = ur;
+            A.out[2 * N + s] = uth;
+            A.out[3 * N + s] = T;
+            A.out[4 * N + s] = lam;
+        }
+        bad |= !isfinite(rho) || !isfinite(ur) || !isfinite(uth) || !isfinite(T) || !isfinite(lam);
+        const double w = (A.r_in + (j + 0.5) * A.dr) * A.dr * A.dtheta;
+        acc[0] += rho * w;
+        acc[1] += rho * ux * w;
+        acc[2] += rho * uy * w;
+        acc[3] += (rho * T + 0.5 * rho * (ux * ux + uy * uy)) * w;
+    }
+    if (bad) atomicOr(A.status, ST_NONFINITE);
+    // deterministic block reduction: warp shuffles, then warp 0 over the warps
+    __shared__ double red[4][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double v = lane < nw ? red[c][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0 && A.partials) A.partials[blockIdx.x * 4 + c] = v;
+        }
+    }
+}
+
+// Sum the per-block partials in a fixed order (one block): totals[4].
+static __global__ void __launch_bounds__(256) totals_kernel(const double *partials, int nblocks, double *totals)
+{
+    __shared__ double red[4][256];
+    for (int c = 0; c < 4; ++c) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[b * 4 + c];
+        red[c][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) totals[threadIdx.x] = red[threadIdx.x][0];
+}
+
+}  // namespace dbm

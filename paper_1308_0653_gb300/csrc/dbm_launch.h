@@ -1,0 +1,27 @@
+// Host-side launch interface between the C-ABI runtime and the kernels of one
+// precision (each precision is its own translation unit, built in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dbm_device.cuh"
+
+namespace dbm {
+
+struct KernelInfo {
+    int W;             // radial sites per CTA (= threads)
+    int nstage;        // row buffers in the shared-memory ring
+    int halo;          // halo columns per side (16 bytes)
+    int smem;          // dynamic shared memory per CTA (bytes)
+    int blocks_per_sm; // resident CTAs per SM at that shared-memory size
+};
+
+template <typename real> cudaError_t kernel_info(KernelInfo *out);
+template <typename real> cudaError_t launch_step(const StepArgs<real> &A, int grid, cudaStream_t s);
+template <typename real> cudaError_t launch_init(const InitArgs<real> &A, cudaStream_t s);
+template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int grid, cudaStream_t s);
+cudaError_t launch_totals(const double *partials, int nblocks, double *totals, cudaStream_t s);
+
+constexpr int MOMENT_BLOCKS = 1024;  // partial-sum slots of the totals reduction
+
+}  // namespace dbm

@@ -1,0 +1,293 @@
+"""ctypes binding of the C ABI in include/dbm.h (argument marshalling only).
+
+Every step of the update runs in the CUDA library ``libdbm.so``; this module
+only converts arguments.  A missing or unloadable library raises; there is no
+CPU fallback.  PyTorch supplies device memory (a uint8 tensor borrowed by the
+library) and streams (``torch.cuda.Stream.cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NV = 33
+DBM_OK, DBM_EINVAL, DBM_ECFL, DBM_ENOMEM, DBM_EBUSY, DBM_ENOTREADY = 0, 1, 2, 3, 4, 5
+DBM_ETIMEOUT, DBM_ENONFINITE, DBM_ECUDA, DBM_ECANCELLED, DBM_ENOTFOUND = 6, 7, 8, 9, 10
+DBM_FP32, DBM_FP64 = 0, 1
+DBM_BC_OUTFLOW = 0
+DBM_R_EXPLICIT, DBM_R_CONSISTENT = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class DbmParams(ctypes.Structure):
+    """Mirror of ``dbm_params``."""
+    _fields_ = [
+        ("nr", ctypes.c_int32), ("ntheta", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("reaction_energy", ctypes.c_int32),
+        ("r_bc_inner", ctypes.c_int32), ("r_bc_outer", ctypes.c_int32),
+        ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+        ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+        ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
+        ("m", ctypes.c_double), ("n", ctypes.c_double), ("T_th", ctypes.c_double),
+        ("v", ctypes.c_double * 4),
+    ]
+
+
+class DbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER(DbmParams)
+        H = ctypes.c_void_p
+        vp = ctypes.c_void_p
+        L.dbm_version.restype = ctypes.c_char_p
+        L.dbm_strerror.argtypes = [ctypes.c_int]
+        L.dbm_strerror.restype = ctypes.c_char_p
+        L.dbm_last_error.restype = ctypes.c_char_p
+        L.dbm_params_default.argtypes = [P]
+        L.dbm_check.argtypes = [P, _dp]
+        L.dbm_state_bytes.argtypes = [P]
+        L.dbm_state_bytes.restype = ctypes.c_size_t
+        L.dbm_create.argtypes = [P, vp, ctypes.c_size_t, ctypes.POINTER(H)]
+        L.dbm_destroy.argtypes = [H]
+        L.dbm_init_state.argtypes = [H] + [_dp] * 5 + [vp]
+        L.dbm_init_state_device.argtypes = [H, vp, vp]
+        L.dbm_step.argtypes = [H, ctypes.c_int64, vp]
+        L.dbm_moments.argtypes = [H] + [_dp] * 6 + [vp]
+        L.dbm_moments_device.argtypes = [H, vp, vp]
+        L.dbm_steps_done.argtypes = [H]
+        L.dbm_steps_done.restype = ctypes.c_int64
+        L.dbm_status.argtypes = [H, vp]
+        L.dbm_export_state.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
+        L.dbm_import_state.argtypes = [H, vp, vp, ctypes.c_int64, vp]
+        L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 5
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().dbm_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != DBM_OK:
+        raise DbmError(status, where)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+def _stream(stream):
+    """cudaStream_t value of a torch stream, an int handle, or None (default)."""
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ---- raw C-ABI entry points (same names) ----------------------------------
+
+def dbm_version() -> str:
+    return lib().dbm_version().decode()
+
+
+def dbm_params_default() -> DbmParams:
+    p = DbmParams()
+    _check(lib().dbm_params_default(ctypes.byref(p)), "dbm_params_default")
+    return p
+
+
+def dbm_check(p: DbmParams):
+    """Returns (status, max Courant sum)."""
+    cfl = ctypes.c_double(0.0)
+    st = lib().dbm_check(ctypes.byref(p), ctypes.byref(cfl))
+    return st, cfl.value
+
+
+def dbm_state_bytes(p: DbmParams) -> int:
+    return int(lib().dbm_state_bytes(ctypes.byref(p)))
+
+
+def dbm_create(p: DbmParams, dev_ptr: int, nbytes: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().dbm_create(ctypes.byref(p), ctypes.c_void_p(dev_ptr), ctypes.c_size_t(nbytes),
+                            ctypes.byref(h)), "dbm_create")
+    return h
+
+
+def dbm_destroy(h):
+    _check(lib().dbm_destroy(h), "dbm_destroy")
+
+
+def dbm_init_state(h, rho, ur, uth, T, lam, stream=None):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ur, uth, T, lam)]
+    _check(lib().dbm_init_state(h, *[_ptr(a) for a in arrs], _stream(stream)), "dbm_init_state")
+
+
+def dbm_init_state_device(h, dev_fields_ptr: int, stream=None):
+    _check(lib().dbm_init_state_device(h, ctypes.c_void_p(dev_fields_ptr), _stream(stream)),
+           "dbm_init_state_device")
+
+
+def dbm_step(h, nsteps: int, stream=None):
+    _check(lib().dbm_step(h, int(nsteps), _stream(stream)), "dbm_step")
+
+
+def dbm_moments(h, rho=None, ur=None, uth=None, T=None, lam=None, totals=None, stream=None,
+                raise_nonfinite=True):
+    st = lib().dbm_moments(h, _ptr(rho), _ptr(ur), _ptr(uth), _ptr(T), _ptr(lam), _ptr(totals),
+                           _stream(stream))
+    if st == DBM_ENONFINITE and not raise_nonfinite:
+        return st
+    _check(st, "dbm_moments")
+    return st
+
+
+def dbm_moments_device(h, dev_out_ptr: int, stream=None):
+    _check(lib().dbm_moments_device(h, ctypes.c_void_p(dev_out_ptr), _stream(stream)),
+           "dbm_moments_device")
+
+
+def dbm_steps_done(h) -> int:
+    return int(lib().dbm_steps_done(h))
+
+
+def dbm_status(h, stream=None) -> int:
+    return int(lib().dbm_status(h, _stream(stream)))
+
+
+def dbm_export_state(h, f, lam, stream=None) -> int:
+    steps = ctypes.c_int64(0)
+    _check(lib().dbm_export_state(h, f.ctypes.data_as(ctypes.c_void_p),
+                                  lam.ctypes.data_as(ctypes.c_void_p), ctypes.byref(steps),
+                                  _stream(stream)), "dbm_export_state")
+    return steps.value
+
+
+def dbm_import_state(h, f, lam, steps: int, stream=None):
+    _check(lib().dbm_import_state(h, f.ctypes.data_as(ctypes.c_void_p),
+                                  lam.ctypes.data_as(ctypes.c_void_p), int(steps),
+                                  _stream(stream)), "dbm_import_state")
+
+
+def dbm_launch_info(h) -> dict:
+    vals = [ctypes.c_int(0) for _ in range(5)]
+    _check(lib().dbm_launch_info(h, *[ctypes.byref(v) for v in vals]), "dbm_launch_info")
+    return dict(zip(("grid", "threads", "smem_bytes", "rows_per_item", "items"),
+                    [v.value for v in vals]))
+
+
+# ---- convenience ----------------------------------------------------------
+
+_PREC = {"fp32": DBM_FP32, "fp64": DBM_FP64, DBM_FP32: DBM_FP32, DBM_FP64: DBM_FP64}
+_RE = {"explicit": DBM_R_EXPLICIT, "consistent": DBM_R_CONSISTENT, 0: 0, 1: 1}
+
+
+def params_from(d: dict) -> DbmParams:
+    """DbmParams from a dict of paper-named parameters (see workloads.py)."""
+    p = dbm_params_default()
+    p.nr, p.ntheta = int(d["nr"]), int(d["ntheta"])
+    for key in ("r_in", "r_out", "dt", "tau", "Q", "omega1", "omega2", "m", "n", "T_th"):
+        if key in d:
+            setattr(p, key, float(d[key]))
+    if "v" in d:
+        for i, val in enumerate(d["v"]):
+            p.v[i] = float(val)
+    p.precision = _PREC[d.get("precision", "fp32")]
+    p.reaction_energy = _RE[d.get("reaction_energy", 0)]
+    p.rows_per_item = int(d.get("rows_per_item", 0))
+    return p
+
+
+FIELDS = ("rho", "ur", "uth", "T", "lam")
+
+
+class Simulation:
+    """One simulation on the current CUDA device; device memory is a torch
+    uint8 tensor that the library borrows for the handle's lifetime."""
+
+    def __init__(self, params, device=None):
+        import torch
+        self.p = params if isinstance(params, DbmParams) else params_from(params)
+        self.nbytes = dbm_state_bytes(self.p)
+        if self.nbytes == 0:
+            raise DbmError(DBM_EINVAL, "dbm_state_bytes")
+        dev = torch.device("cuda" if device is None else device)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) // 256 * 256
+        self.h = dbm_create(self.p, self.ptr, self.nbytes)
+
+    @property
+    def shape(self):
+        return (self.p.ntheta, self.p.nr)
+
+    def init_state(self, fields: dict, stream=None):
+        dbm_init_state(self.h, *[fields[k] for k in FIELDS], stream=stream)
+
+    def step(self, nsteps: int, stream=None):
+        dbm_step(self.h, nsteps, stream)
+
+    def moments(self, stream=None, totals=False, raise_nonfinite=True):
+        out = {k: np.empty(self.shape) for k in FIELDS}
+        tot = np.zeros(4) if totals else None
+        st = dbm_moments(self.h, *[out[k] for k in FIELDS], totals=tot, stream=stream,
+                         raise_nonfinite=raise_nonfinite)
+        if totals:
+            out["totals"] = tot
+        out["status"] = st
+        return out
+
+    def launch_info(self) -> dict:
+        return dbm_launch_info(self.h)
+
+    def export_state(self, stream=None):
+        dt = np.float64 if self.p.precision == DBM_FP64 else np.float32
+        f = np.empty((NV, self.p.ntheta, self.p.nr), dtype=dt)
+        lam = np.empty((self.p.ntheta, self.p.nr), dtype=dt)
+        steps = dbm_export_state(self.h, f, lam, stream)
+        return f, lam, steps
+
+    def import_state(self, f, lam, steps, stream=None):
+        dt = np.float64 if self.p.precision == DBM_FP64 else np.float32
+        f = np.ascontiguousarray(f, dtype=dt)
+        lam = np.ascontiguousarray(lam, dtype=dt)
+        dbm_import_state(self.h, f, lam, steps, stream)
+
+    def close(self):
+        if self.h is not None:
+            dbm_destroy(self.h)
+            self.h = None
+            self.buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,143 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs: FP64 within 1e-11 and FP32 within 1e-4 relative L-inf,
+on the paper-shaped workloads at oracle-friendly sizes, at full size for a
+few steps in the benchmark's launch shape, and on ragged and degenerate grids.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import FIELDS, TOL, assert_close, oracle_params, rel_errors, run_gpu, run_oracle
+from paper_1308_0653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_explosion64_full_run(orc, precision):
+    """64 x 64 non-reactive explosion, 200 steps (the small FP64 config)."""
+    w = W.explosion64()
+    ref = run_oracle(orc, w)
+    out = run_gpu(w, precision)
+    assert_close(out, ref, TOL[precision], f"explosion64 {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_reactive_explosion_128(orc, precision):
+    """Reactive explosion (hot reacted ring, Cochran rate with ignition gate,
+    1 % seeded density noise) on 128 x 128, 600 steps: every term active."""
+    w = W.explosion(128, 128, nsteps=600, seed=0, dt=2e-5)
+    ref = run_oracle(orc, w)
+    assert ref["lam"].max() > 0.99 and ref["lam"].min() < 0.01
+    out = run_gpu(w, precision)
+    assert_close(out, ref, TOL[precision], f"explosion128 {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_reactive_explosion_512_full(orc, precision):
+    """The 512 x 512 reactive explosion for its full 5000 steps."""
+    w = W.explosion(512, 512, nsteps=5000, seed=0)
+    ref = run_oracle(orc, w)
+    out = run_gpu(w, precision)
+    assert_close(out, ref, TOL[precision], f"explosion512 {precision}")
+
+
+def test_implosion_2048_in_bench_launch_shape(orc):
+    """2048 x 2048 reactive implosion, FP32, 4 steps, in the launch shape the
+    benchmark times (automatic rows per item, persistent grid)."""
+    w = W.implosion(2048, 2048, nsteps=4, seed=0)
+    ref = run_oracle(orc, w)
+    out = run_gpu(w, "fp32")
+    assert out["launch"]["threads"] == 128
+    assert_close(out, ref, TOL["fp32"], "implosion2048 fp32")
+
+
+@pytest.mark.parametrize("nr,nth,rows", [(1, 8, 0), (5, 3, 0), (100, 7, 0), (130, 16, 1),
+                                         (257, 9, 4), (33, 1, 0), (64, 2, 0), (96, 24, 1000),
+                                         (200, 40, 3)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_ragged_and_degenerate_grids(orc, nr, nth, rows, precision):
+    """Ragged radial tails (nr not a multiple of the 128/64-site strip),
+    ntheta not a multiple of 8 (direct angles), ntheta = 1 and 2 (a row is its
+    own theta neighbour), nr = 1 (both radial ghosts), and forced rows per item."""
+    w = W.random_smooth(nr, nth, seed=nr + nth, amp=0.1, r_in=0.5, r_out=1.5, omega1=3.0,
+                        omega2=5.0, dt=2e-4, tau=5e-4)
+    w.fields["T"] = w.fields["T"] * 0.9  # straddle the ignition temperature
+    ref = run_oracle(orc, w, nsteps=25)
+    out = run_gpu(w, precision, nsteps=25, rows_per_item=rows)
+    assert_close(out, ref, TOL[precision], f"{nr}x{nth} rows={rows} {precision}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_consistent_reaction_energy_and_general_exponents(orc, precision):
+    """Options: R taken as the step's lambda increment, and Cochran exponents
+    m, n other than 1 (pow path)."""
+    w = W.explosion(64, 32, nsteps=100, seed=3, dt=4e-5)
+    ref = run_oracle(orc, w, reaction_energy=1, m=1.5, n=0.7)
+    out = run_gpu(w, precision, reaction_energy=1, m=1.5, n=0.7)
+    assert_close(out, ref, TOL[precision], f"consistent {precision}")
+
+
+def test_totals_match_the_oracle(orc):
+    w = W.explosion(96, 64, nsteps=50, seed=1, dt=2e-5)
+    p = oracle_params(orc, w)
+    f, lam = orc.init(p, w.fields)
+    for _ in range(50):
+        f, lam, _ = orc.step(p, f, lam)
+    tot = orc.totals(p, f)
+    out = run_gpu(w, "fp64")
+    np.testing.assert_allclose(out["totals"], tot, rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_uniform_state_stays_uniform(precision):
+    """A uniform moving state is a fixed point of the update (every difference
+    vanishes and f = f^eq), over 500 steps."""
+    w = W.uniform_state(200, 64, 1.3, 0.3, -0.2, 1.2, 0.4, dt=1e-5)
+    out = run_gpu(w, precision, nsteps=500)
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for k in FIELDS:
+        np.testing.assert_allclose(out[k], w.fields[k], atol=tol * max(1.0, np.abs(w.fields[k]).max()))
+
+
+def test_rotation_by_pi_over_4_fp32():
+    """8-fold rotation equivariance on the GPU: rotating the initial data by
+    pi/4 rotates the result (FP32, to round-off)."""
+    w = W.random_smooth(64, 64, seed=9, amp=0.1, dt=2e-5, omega1=2.0, omega2=2.0)
+    rot = W.Workload(w.name, w.params, {k: np.ascontiguousarray(np.roll(v, 8, axis=0))
+                                        for k, v in w.fields.items()}, 0)
+    a = run_gpu(w, "fp32", nsteps=100)
+    b = run_gpu(rot, "fp32", nsteps=100)
+    for k in FIELDS:
+        np.testing.assert_allclose(np.roll(a[k], 8, axis=0), b[k], atol=2e-6, rtol=0)
+
+
+def test_graph_and_single_launches_are_bitwise_identical():
+    """dbm_step(n) replays a captured CUDA graph for runs of 32 steps; the
+    result equals n single-step calls bit for bit."""
+    from paper_1308_0653_gb300 import dbm
+    w = W.explosion(160, 48, nsteps=0, seed=2, dt=2e-5)
+    outs = []
+    for chunks in ([70], [1] * 70):
+        sim = dbm.Simulation(dict(w.params, precision="fp32"))
+        sim.init_state(w.fields)
+        for c in chunks:
+            sim.step(c)
+        assert dbm.dbm_steps_done(sim.h) == 70
+        outs.append(sim.export_state())
+        sim.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_zero_steps_is_a_noop(orc):
+    w = W.explosion(32, 16, nsteps=0, seed=4)
+    out = run_gpu(w, "fp64", nsteps=0)
+    ref = run_oracle(orc, w, nsteps=0)
+    assert_close(out, ref, 1e-13, "zero steps")

@@ -1,0 +1,129 @@
+"""Runtime behaviour of the C ABI on the GPU: checkpoint/resume, error
+statuses made on the host (no GPU fault is ever provoked), streams."""
+import numpy as np
+import pytest
+
+from paper_1308_0653_gb300 import dbm
+from paper_1308_0653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(precision):
+    """Export after 37 steps, import into a fresh handle, run 40 more: equal
+    bit for bit to 77 uninterrupted steps."""
+    w = W.explosion(96, 40, nsteps=0, seed=5, dt=2e-5)
+    a = dbm.Simulation(dict(w.params, precision=precision))
+    a.init_state(w.fields)
+    a.step(77)
+    fa, la, sa = a.export_state()
+    a.close()
+    b = dbm.Simulation(dict(w.params, precision=precision))
+    b.init_state(w.fields)
+    b.step(37)
+    f, lam, s = b.export_state()
+    assert s == 37
+    b.close()
+    c = dbm.Simulation(dict(w.params, precision=precision))
+    c.import_state(f, lam, s)
+    c.step(40)
+    fc, lc, sc = c.export_state()
+    c.close()
+    assert sc == sa == 77
+    assert np.array_equal(fa, fc) and np.array_equal(la, lc)
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN planted on the host (imported state) is reported by dbm_moments
+    as DBM_ENONFINITE after a step, not as a crash."""
+    w = W.explosion(64, 16, nsteps=0, seed=6)
+    sim = dbm.Simulation(dict(w.params, precision="fp32"))
+    sim.init_state(w.fields)
+    f, lam, s = sim.export_state()
+    f[3, 5, 7] = np.nan
+    sim.import_state(f, lam, s)
+    sim.step(2)
+    out = sim.moments(raise_nonfinite=False)
+    assert out["status"] == dbm.DBM_ENONFINITE
+    assert np.isnan(out["rho"]).any()
+    assert dbm.dbm_status(sim.h) == dbm.DBM_OK
+    sim.close()
+
+
+def test_invalid_initial_fields_are_rejected():
+    w = W.explosion(32, 8, nsteps=0, seed=7)
+    sim = dbm.Simulation(dict(w.params, precision="fp32"))
+    bad = dict(w.fields)
+    bad["T"] = bad["T"].copy()
+    bad["T"][2, 3] = -1.0
+    with pytest.raises(dbm.DbmError) as e:
+        sim.init_state(bad)
+    assert e.value.status == dbm.DBM_EINVAL
+    bad["T"][2, 3] = np.inf
+    with pytest.raises(dbm.DbmError):
+        sim.init_state(bad)
+    sim.close()
+
+
+def test_buffer_too_small_and_courant_violation():
+    import torch
+    p = dbm.params_from(W.explosion(64, 64, nsteps=0).params)
+    need = dbm.dbm_state_bytes(p)
+    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dbm.DbmError) as e:
+        dbm.dbm_create(p, buf.data_ptr(), need - 256)
+    assert e.value.status == dbm.DBM_ENOMEM
+    p.dt = 1e-3
+    with pytest.raises(dbm.DbmError) as e:
+        dbm.dbm_create(p, buf.data_ptr(), need)
+    assert e.value.status == dbm.DBM_ECFL
+
+
+def test_work_on_a_side_stream_matches_default_stream():
+    import torch
+    w = W.explosion(128, 64, nsteps=40, seed=8, dt=2e-5)
+    a = dbm.Simulation(dict(w.params, precision="fp32"))
+    a.init_state(w.fields)
+    a.step(40)
+    ra = a.moments()
+    a.close()
+    s = torch.cuda.Stream()
+    b = dbm.Simulation(dict(w.params, precision="fp32"))
+    b.init_state(w.fields, stream=s)
+    b.step(40, stream=s)
+    rb = b.moments(stream=s)
+    b.close()
+    for k in ("rho", "ur", "uth", "T", "lam"):
+        assert np.array_equal(ra[k], rb[k])
+
+
+def test_device_resident_init_and_moments(orc):
+    """dbm_init_state_device / dbm_moments_device give the same result as the
+    host-array calls."""
+    import torch
+    w = W.explosion(96, 32, nsteps=30, seed=9, dt=2e-5)
+    host = dbm.Simulation(dict(w.params, precision="fp64"))
+    host.init_state(w.fields)
+    host.step(30)
+    rh = host.moments()
+    host.close()
+    dev = dbm.Simulation(dict(w.params, precision="fp64"))
+    fields = torch.from_numpy(np.stack([w.fields[k] for k in ("rho", "ur", "uth", "T", "lam")])).cuda()
+    dbm.dbm_init_state_device(dev.h, fields.data_ptr())
+    dbm.dbm_step(dev.h, 30)
+    out = torch.empty_like(fields)
+    dbm.dbm_moments_device(dev.h, out.data_ptr())
+    torch.cuda.synchronize()
+    res = out.cpu().numpy()
+    dev.close()
+    for c, k in enumerate(("rho", "ur", "uth", "T", "lam")):
+        assert np.array_equal(res[c], rh[k])
