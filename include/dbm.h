@@ -187,6 +187,64 @@ int dbm_import_state(dbm_t *h, const void *f, const void *lam, int64_t steps, vo
 int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes,
                     int *rows_per_item, int *items);
 
+/* ---- batches: many uneven simulations, one persistent launch per step ---- */
+/*
+ * A batch advances the simulations attached to its slots together: each time
+ * step is ONE launch of the persistent step kernel over a device table of
+ * work items (W radial sites x rows_per_item theta rows) drawn from every
+ * attached simulation, interleaved so that every CTA gets a share of each.
+ * A device-side step counter T decides which slots are active in a step
+ * (slot s advances while start_s <= T < end_s), so a captured CUDA graph of
+ * 32 steps stays valid while slots come and go.  The update of each
+ * simulation is exactly the single-instance update (same kernel body).
+ * All simulations of a batch share one precision.  While attached, a
+ * simulation must not be stepped on its own.
+ */
+typedef struct dbm_batch_s dbm_batch_t;
+
+/* Host-only: device bytes for a batch of max_slots slots and at most
+ * max_items work items (0 if an argument is invalid). */
+size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
+
+/* Create a batch on caller device memory (256-byte aligned, >=
+ * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16).
+ * Allocates a pinned host staging buffer for the tables.  Synchronous.
+ * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
+int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
+                     void *dev_buf, size_t dev_bytes, dbm_batch_t **out);
+
+/* Free the batch (not the attached simulations or dev_buf). */
+int dbm_batch_destroy(dbm_batch_t *b);
+
+/* Attach simulation h to a free slot to advance nsteps steps from the batch's
+ * current step on (it keeps its own state buffers).  Takes effect at the next
+ * dbm_batch_step.  Errors: DBM_EINVAL (bad slot, precision mismatch, h
+ * already attached), DBM_EBUSY (slot taken). */
+int dbm_batch_attach(dbm_batch_t *b, int slot, dbm_t *h, int64_t nsteps);
+
+/* Free a slot; the simulation keeps the steps it took (its step counter and
+ * buffer index are up to date after every dbm_batch_step).
+ * Errors: DBM_EINVAL, DBM_ENOTFOUND (slot empty). */
+int dbm_batch_detach(dbm_batch_t *b, int slot);
+
+/* Steps the slot's simulation still has to take (-1 if the slot is empty). */
+int64_t dbm_batch_remaining(const dbm_batch_t *b, int slot);
+
+/* The batch's step counter T (host view). */
+int64_t dbm_batch_time(const dbm_batch_t *b);
+
+/* Upload the slot and item tables (stream-ordered; done automatically by
+ * dbm_batch_step after attach/detach).  Errors: DBM_ENOMEM (more items than
+ * max_items), DBM_ECUDA. */
+int dbm_batch_commit(dbm_batch_t *b, void *stream);
+
+/* Advance the step counter nsteps steps on `stream` (asynchronous); every
+ * attached simulation advances while it has steps left. */
+int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
+
+/* Launch shape: persistent grid, current number of work items, rows per item. */
+int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item);
+
 #ifdef __cplusplus
 }
 #endif

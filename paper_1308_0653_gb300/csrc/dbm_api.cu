@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
+#include <vector>
 
 #include "dbm.h"
 #include "dbm_launch.h"
@@ -631,6 +633,351 @@ int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes, in
     if (smem_bytes) *smem_bytes = h->ki.smem;
     if (rows_per_item) *rows_per_item = h->rows_per_item;
     if (items) *items = h->items;
+    return DBM_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many uneven instances advanced by one persistent launch per step.
+// ===========================================================================
+struct dbm_batch_s {
+    int precision;
+    int max_slots;
+    long long max_items;
+    int rows_per_item;
+    unsigned char *buf;
+    size_t bytes;
+    size_t off_slots, off_items, off_nitems, off_T, total;
+    size_t slot_bytes;
+    std::vector<dbm_t *> inst;
+    std::vector<long long> start, end;
+    std::vector<int> par0;
+    unsigned char *stage;     // pinned host staging of the slot and item tables
+    cudaEvent_t stage_ev;
+    bool stage_pending;
+    long long T;              // host mirror of the device step counter
+    int n_items;
+    bool dirty;
+    KernelInfo ki;
+    int grid;
+    cudaGraphExec_t graph;    // GRAPH_STEPS batch steps + counter advance
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t slot_bytes, slots, items, nitems, T, total;
+};
+
+BatchLayout batch_layout(int max_slots, long long max_items, int precision)
+{
+    BatchLayout L;
+    L.slot_bytes = precision == DBM_FP64 ? sizeof(BatchSlot<double>) : sizeof(BatchSlot<float>);
+    size_t off = 0;
+    L.slots = off;
+    off = align256(off + (size_t)max_slots * L.slot_bytes);
+    L.items = off;
+    off = align256(off + (size_t)max_items * sizeof(int4));
+    L.nitems = off;
+    off = align256(off + sizeof(int));
+    L.T = off;
+    off = align256(off + sizeof(long long));
+    L.total = off;
+    return L;
+}
+
+template <typename real>
+void fill_slot(dbm_batch_t *b, int s, unsigned char *dst)
+{
+    BatchSlot<real> sl;
+    std::memset(&sl, 0, sizeof(sl));
+    if (b->inst[s]) {
+        const StepArgs<real> *a;
+        if constexpr (std::is_same<real, double>::value)
+            a = b->inst[s]->a64;
+        else
+            a = b->inst[s]->a32;
+        sl.args[0] = a[0];
+        sl.args[1] = a[1];
+        sl.start = b->start[s];
+        sl.end = b->end[s];
+        sl.par0 = b->par0[s];
+    } else {
+        sl.start = 0;
+        sl.end = 0;  // never active
+    }
+    std::memcpy(dst, &sl, sizeof(sl));
+}
+
+int batch_launch(dbm_batch_t *b, int s, cudaStream_t st)
+{
+    cudaError_t e;
+    if (b->precision == DBM_FP64) {
+        BatchArgs<double> B{reinterpret_cast<const BatchSlot<double> *>(b->buf + b->off_slots),
+                            reinterpret_cast<const int4 *>(b->buf + b->off_items),
+                            reinterpret_cast<const int *>(b->buf + b->off_nitems),
+                            reinterpret_cast<const long long *>(b->buf + b->off_T), s};
+        e = launch_batch_step<double>(B, b->grid, st);
+    } else {
+        BatchArgs<float> B{reinterpret_cast<const BatchSlot<float> *>(b->buf + b->off_slots),
+                           reinterpret_cast<const int4 *>(b->buf + b->off_items),
+                           reinterpret_cast<const int *>(b->buf + b->off_nitems),
+                           reinterpret_cast<const long long *>(b->buf + b->off_T), s};
+        e = launch_batch_step<float>(B, b->grid, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch step kernel launch");
+    return DBM_OK;
+}
+
+int batch_advance(dbm_batch_t *b, int k, cudaStream_t st)
+{
+    cudaError_t e = launch_batch_advance(reinterpret_cast<long long *>(b->buf + b->off_T), k, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch advance launch");
+    return DBM_OK;
+}
+
+int batch_build_graph(dbm_batch_t *b)
+{
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int rc = DBM_OK;
+    if (e == cudaSuccess) {
+        for (int s = 0; s < GRAPH_STEPS && rc == DBM_OK; ++s) rc = batch_launch(b, s, cs);
+        if (rc == DBM_OK) rc = batch_advance(b, GRAPH_STEPS, cs);
+        e = cudaStreamEndCapture(cs, &g);
+    }
+    if (e == cudaSuccess && rc == DBM_OK) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (rc != DBM_OK) return rc;
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return cuda_fail(e, "batch graph capture");
+    }
+    return DBM_OK;
+}
+
+// Host bookkeeping of an attached instance after the clock moved t0 -> t1.
+void batch_account(dbm_batch_t *b, int s, long long t0, long long t1)
+{
+    dbm_t *h = b->inst[s];
+    if (!h) return;
+    const long long a0 = std::min(std::max(t0, b->start[s]), b->end[s]);
+    const long long a1 = std::min(std::max(t1, b->start[s]), b->end[s]);
+    h->steps += a1 - a0;
+    h->cur = (int)((b->par0[s] + (a1 - b->start[s])) & 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision)
+{
+    if (max_slots < 1 || max_items < 1 || (precision != DBM_FP32 && precision != DBM_FP64)) return 0;
+    return batch_layout(max_slots, max_items, precision).total;
+}
+
+int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
+                     void *dev_buf, size_t dev_bytes, dbm_batch_t **out)
+{
+    if (!out || !dev_buf || max_slots < 1 || max_items < 1 || max_items > (1LL << 31) ||
+        rows_per_item < 0 || (precision != DBM_FP32 && precision != DBM_FP64))
+        return DBM_EINVAL;
+    *out = nullptr;
+    if (((uintptr_t)dev_buf & 255) != 0) return DBM_EINVAL;
+    const BatchLayout L = batch_layout(max_slots, max_items, precision);
+    if (dev_bytes < L.total) return DBM_ENOMEM;
+    dbm_batch_t *b = new (std::nothrow) dbm_batch_t();
+    if (!b) return DBM_ENOMEM;
+    b->precision = precision;
+    b->max_slots = max_slots;
+    b->max_items = max_items;
+    b->rows_per_item = rows_per_item > 0 ? rows_per_item : 16;
+    b->buf = static_cast<unsigned char *>(dev_buf);
+    b->bytes = dev_bytes;
+    b->off_slots = L.slots;
+    b->off_items = L.items;
+    b->off_nitems = L.nitems;
+    b->off_T = L.T;
+    b->total = L.total;
+    b->slot_bytes = L.slot_bytes;
+    b->inst.assign(max_slots, nullptr);
+    b->start.assign(max_slots, 0);
+    b->end.assign(max_slots, 0);
+    b->par0.assign(max_slots, 0);
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = precision == DBM_FP64 ? batch_kernel_info<double>(&b->ki) : batch_kernel_info<float>(&b->ki);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->stage, L.items + (size_t)max_items * sizeof(int4) + 256,
+                                            cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemset(dev_buf, 0, L.total);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        if (b->stage) cudaFreeHost(b->stage);
+        delete b;
+        return cuda_fail(e, "dbm_batch_create");
+    }
+    b->grid = nsm * std::max(1, b->ki.blocks_per_sm);
+    b->dirty = true;
+    *out = b;
+    return DBM_OK;
+}
+
+int dbm_batch_destroy(dbm_batch_t *b)
+{
+    if (!b) return DBM_EINVAL;
+    if (b->stage_pending) cudaEventSynchronize(b->stage_ev);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaEventDestroy(b->stage_ev);
+    cudaFreeHost(b->stage);
+    delete b;
+    return DBM_OK;
+}
+
+int dbm_batch_attach(dbm_batch_t *b, int slot, dbm_t *h, int64_t nsteps)
+{
+    if (!b || !h || slot < 0 || slot >= b->max_slots || nsteps < 0) return DBM_EINVAL;
+    if (b->inst[slot]) return DBM_EBUSY;
+    if (h->p.precision != b->precision) return DBM_EINVAL;
+    for (int s = 0; s < b->max_slots; ++s)
+        if (b->inst[s] == h) return DBM_EINVAL;
+    b->inst[slot] = h;
+    b->start[slot] = b->T;
+    b->end[slot] = b->T + nsteps;
+    b->par0[slot] = h->cur;
+    b->dirty = true;
+    return DBM_OK;
+}
+
+int dbm_batch_detach(dbm_batch_t *b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_slots) return DBM_EINVAL;
+    if (!b->inst[slot]) return DBM_ENOTFOUND;
+    b->inst[slot] = nullptr;
+    b->dirty = true;
+    return DBM_OK;
+}
+
+int64_t dbm_batch_remaining(const dbm_batch_t *b, int slot)
+{
+    if (!b || slot < 0 || slot >= b->max_slots || !b->inst[slot]) return -1;
+    return std::max(0LL, b->end[slot] - std::max(b->T, b->start[slot]));
+}
+
+int64_t dbm_batch_time(const dbm_batch_t *b) { return b ? b->T : -1; }
+
+int dbm_batch_commit(dbm_batch_t *b, void *stream)
+{
+    if (!b) return DBM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // item table: W sites x rows_per_item rows of every attached instance
+    long long n = 0;
+    for (int s = 0; s < b->max_slots; ++s) {
+        if (!b->inst[s]) continue;
+        const dbm_params &p = b->inst[s]->p;
+        const long long strips = (p.nr + b->ki.W - 1) / b->ki.W;
+        const long long segs = (p.ntheta + b->rows_per_item - 1) / b->rows_per_item;
+        n += strips * segs;
+    }
+    if (n > b->max_items) return DBM_ENOMEM;
+    if (b->stage_pending) {
+        CK(cudaEventSynchronize(b->stage_ev));
+        b->stage_pending = false;
+    }
+    unsigned char *slots = b->stage;
+    int4 *items = reinterpret_cast<int4 *>(b->stage + b->off_items);
+    for (int s = 0; s < b->max_slots; ++s) {
+        if (b->precision == DBM_FP64)
+            fill_slot<double>(b, s, slots + (size_t)s * b->slot_bytes);
+        else
+            fill_slot<float>(b, s, slots + (size_t)s * b->slot_bytes);
+    }
+    // interleave the instances' items so every CTA gets a share of each
+    std::vector<long long> cursor(b->max_slots, 0), count(b->max_slots, 0);
+    for (int s = 0; s < b->max_slots; ++s) {
+        if (!b->inst[s]) continue;
+        const dbm_params &p = b->inst[s]->p;
+        count[s] = (long long)((p.nr + b->ki.W - 1) / b->ki.W) *
+                   ((p.ntheta + b->rows_per_item - 1) / b->rows_per_item);
+    }
+    long long k = 0;
+    bool more = true;
+    while (more) {
+        more = false;
+        for (int s = 0; s < b->max_slots; ++s) {
+            if (cursor[s] >= count[s]) continue;
+            const dbm_params &p = b->inst[s]->p;
+            const int strips = (p.nr + b->ki.W - 1) / b->ki.W;
+            const long long it = cursor[s]++;
+            const int strip = (int)(it % strips), seg = (int)(it / strips);
+            const int mb = seg * b->rows_per_item;
+            items[k++] = make_int4(s, strip * b->ki.W, mb, std::min(mb + b->rows_per_item, p.ntheta));
+            more = true;
+        }
+    }
+    b->n_items = (int)n;
+    std::memcpy(b->stage + b->off_nitems, &b->n_items, sizeof(int));
+    CK(cudaMemcpyAsync(b->buf + b->off_slots, b->stage, (size_t)b->max_slots * b->slot_bytes,
+                       cudaMemcpyHostToDevice, st));
+    if (n > 0)
+        CK(cudaMemcpyAsync(b->buf + b->off_items, b->stage + b->off_items, (size_t)n * sizeof(int4),
+                           cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->buf + b->off_nitems, b->stage + b->off_nitems, sizeof(int),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(b->stage_ev, st));
+    b->stage_pending = true;
+    b->dirty = false;
+    return DBM_OK;
+}
+
+int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream)
+{
+    if (!b || nsteps < 0) return DBM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (b->dirty) {
+        int rc = dbm_batch_commit(b, stream);
+        if (rc != DBM_OK) return rc;
+    }
+    const long long t0 = b->T;
+    while (nsteps > 0) {
+        int rc;
+        if (nsteps >= GRAPH_STEPS) {
+            if (!b->graph) {
+                rc = batch_build_graph(b);
+                if (rc != DBM_OK) return rc;
+            }
+            CK(cudaGraphLaunch(b->graph, st));
+            nsteps -= GRAPH_STEPS;
+            b->T += GRAPH_STEPS;
+        } else {
+            const int k = (int)nsteps;
+            for (int s = 0; s < k; ++s) {
+                rc = batch_launch(b, s, st);
+                if (rc != DBM_OK) return rc;
+            }
+            rc = batch_advance(b, k, st);
+            if (rc != DBM_OK) return rc;
+            nsteps = 0;
+            b->T += k;
+        }
+    }
+    for (int s = 0; s < b->max_slots; ++s) batch_account(b, s, t0, b->T);
+    return DBM_OK;
+}
+
+int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item)
+{
+    if (!b) return DBM_EINVAL;
+    if (grid) *grid = b->grid;
+    if (items) *items = b->n_items;
+    if (rows_per_item) *rows_per_item = b->rows_per_item;
     return DBM_OK;
 }
 

@@ -136,20 +136,6 @@ template <> __device__ __forceinline__ float pow_<float>(float x, float y) { ret
 template <> __device__ __forceinline__ double pow_<double>(double x, double y) { return pow(x, y); }
 
 // ---------------------------------------------------------------------------
-// Work-item decoding: item -> (strip j0, rows [mb, me))
-// ---------------------------------------------------------------------------
-template <typename real, int W>
-__device__ __forceinline__ void decode_item(const StepArgs<real> &A, int item, int &j0, int &mb,
-                                            int &me)
-{
-    const int strip = item % A.strips;
-    const int seg = item / A.strips;
-    j0 = strip * W;
-    mb = seg * A.rows_per_item;
-    me = min(mb + A.rows_per_item, A.ntheta);
-}
-
-// ---------------------------------------------------------------------------
 // One site's update (Eq. LB_evolution_equation, Eq. Eqlambda), all 33
 // velocities unrolled.  sp/sc/sn: shared-memory buffers of rows m-1, m, m+1;
 // col = HALO + tx.  Velocity (k, i) has Cartesian direction i pi / 4, so its
@@ -299,17 +285,85 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
 }
 
 // ---------------------------------------------------------------------------
-// The fused persistent step kernel.
+// Work lists.  A work item is W radial sites x a run of theta rows of one
+// instance.  SingleWork decodes items of one instance arithmetically (its
+// arguments live in kernel parameter space); BatchWork reads items of many
+// uneven instances from a device table and decides on the device, from the
+// global step counter T, which instances are active in this step.
 // ---------------------------------------------------------------------------
-template <typename real, int W, int NSTAGE>
-__global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ StepArgs<real> A)
+template <typename real, int W>
+struct SingleWork {
+    static constexpr bool kCopyArgs = false;
+    const StepArgs<real> *A;
+    __device__ __forceinline__ int count() const { return A->items; }
+    __device__ __forceinline__ bool item(int it, const StepArgs<real> *&a, int &j0, int &mb,
+                                         int &me) const
+    {
+        a = A;
+        const int strip = it % A->strips;
+        const int seg = it / A->strips;
+        j0 = strip * W;
+        mb = seg * A->rows_per_item;
+        me = min(mb + A->rows_per_item, A->ntheta);
+        return true;
+    }
+};
+
+// One batch slot: the instance's step arguments for both ping-pong parities
+// and the global steps [start, end) during which it advances.
+template <typename real>
+struct BatchSlot {
+    StepArgs<real> args[2];  // [p]: reads buffer p, writes buffer 1 - p
+    long long start, end;
+    int par0;                // the instance's buffer index at global step start
+    int pad;
+};
+
+template <typename real>
+struct BatchArgs {
+    const BatchSlot<real> *slots;
+    const int4 *items;        // (slot, j0, mb, me)
+    const int *n_items;       // device word: number of valid items
+    const long long *T;       // device word: global step at the start of this replay
+    int s;                    // step index within the replay
+};
+
+template <typename real, int W>
+struct BatchWork {
+    static constexpr bool kCopyArgs = true;
+    const BatchSlot<real> *slots;
+    const int4 *items;
+    int n;
+    long long T;
+    __device__ __forceinline__ int count() const { return n; }
+    __device__ __forceinline__ bool item(int it, const StepArgs<real> *&a, int &j0, int &mb,
+                                         int &me) const
+    {
+        const int4 e = items[it];
+        const BatchSlot<real> &sl = slots[e.x];
+        if (T < sl.start || T >= sl.end) return false;
+        a = &sl.args[(int)((T - sl.start + sl.par0) & 1)];
+        j0 = e.y;
+        mb = e.z;
+        me = e.w;
+        return true;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The fused persistent step: march over this CTA's work items (items
+// blockIdx.x, blockIdx.x + gridDim.x, ...), keeping the TMA row ring full
+// across item boundaries.
+// ---------------------------------------------------------------------------
+template <typename real, int W, int NSTAGE, typename Work>
+__device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
+                                      StepArgs<real> *sargs)
 {
     constexpr int HALO = Halo<real>::value;
     constexpr int WP = W + 2 * HALO;
     constexpr int SLOT = NARR * WP;  // elements per row buffer
     static_assert(NSTAGE >= 3, "rows m-1, m, m+1 must be resident");
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     real *sm = reinterpret_cast<real *>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + sizeof(real) * NSTAGE * SLOT);
     __shared__ int abort_flag;
@@ -317,6 +371,7 @@ __global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ Step
     const int tx = threadIdx.x;
     const int lane = tx & 31;
     const bool producer = tx < 32;  // warp 0 issues the copies
+    const int nitems = work.count();
 
     if (tx == 0) {
         for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
@@ -325,39 +380,46 @@ __global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ Step
     }
     __syncthreads();
 
-    // Total row loads of this CTA: rows mb-1 .. me for each of its items.
+    // Total row loads of this CTA: rows mb-1 .. me of each active item.
     long long total_loads = 0;
-    for (int it = blockIdx.x; it < A.items; it += gridDim.x) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const StepArgs<real> *a;
         int j0, mb, me;
-        decode_item<real, W>(A, it, j0, mb, me);
-        total_loads += (me - mb) + 2;
+        if (work.item(it, a, j0, mb, me)) total_loads += (me - mb) + 2;
     }
 
     // Producer cursor (replicated in the lanes of warp 0).
     long long issued = 0;
     int p_item = blockIdx.x, p_row = 0;
+    const StepArgs<real> *pa = nullptr;
+    int pj0 = 0, pmb = 0, pme = 0;
+    bool p_ok = false;
 
     auto issue_one = [&]() {
-        int j0, mb, me;
-        decode_item<real, W>(A, p_item, j0, mb, me);
-        int m = mb - 1 + p_row;
-        m = m < 0 ? m + A.ntheta : (m >= A.ntheta ? m - A.ntheta : m);
+        while (!p_ok) {  // find the next active item
+            p_ok = work.item(p_item, pa, pj0, pmb, pme);
+            if (!p_ok) p_item += gridDim.x;
+        }
+        int m = pmb - 1 + p_row;
+        const int nth = pa->ntheta;
+        m = m < 0 ? m + nth : (m >= nth ? m - nth : m);
         const int slot = (int)(issued % NSTAGE);
-        const int jlo = max(j0 - HALO, 0);
-        const int jhi = min(j0 + W + HALO, A.ld);
+        const int jlo = max(pj0 - HALO, 0);
+        const int jhi = min(pj0 + W + HALO, pa->ld);
         const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
-        real *dst = sm + slot * SLOT + (jlo - (j0 - HALO));
+        real *dst = sm + slot * SLOT + (jlo - (pj0 - HALO));
         if (lane == 0) mbar_arrive_expect_tx(&bars[slot], nbytes * NARR);
         __syncwarp();
+        const long long roff = (long long)m * pa->ld + jlo;
         for (int a = lane; a < NARR; a += 32) {
-            const real *src = (a < NV) ? A.f_in + (long long)a * A.plane + (long long)m * A.ld + jlo
-                                       : A.lam_in + (long long)m * A.ld + jlo;
+            const real *src = (a < NV) ? pa->f_in + (long long)a * pa->plane + roff : pa->lam_in + roff;
             bulk_g2s(dst + a * WP, src, nbytes, &bars[slot]);
         }
         ++issued;
-        if (++p_row == (me - mb) + 2) {
+        if (++p_row == (pme - pmb) + 2) {
             p_row = 0;
             p_item += gridDim.x;
+            p_ok = false;
         }
     };
 
@@ -367,9 +429,20 @@ __global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ Step
 
     long long base = 0;  // sequence position of the current item's first load
     bool ok = true;
-    for (int it = blockIdx.x; it < A.items && ok; it += gridDim.x) {
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        const StepArgs<real> *ga;
         int j0, mb, me;
-        decode_item<real, W>(A, it, j0, mb, me);
+        if (!work.item(it, ga, j0, mb, me)) continue;
+        const StepArgs<real> *ap = ga;
+        if constexpr (Work::kCopyArgs) {
+            // per-instance constants into shared memory (read by every thread)
+            const int nw = (int)(sizeof(StepArgs<real>) / sizeof(int));
+            for (int q = tx; q < nw; q += blockDim.x)
+                reinterpret_cast<int *>(sargs)[q] = reinterpret_cast<const int *>(ga)[q];
+            __syncthreads();
+            ap = sargs;
+        }
+        const StepArgs<real> &A = *ap;
         const int L = me - mb;
         const int j = j0 + tx;
         const bool active = j < A.nr;
@@ -415,8 +488,32 @@ __global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ Step
 
     if (!ok && tx == 0) {
         // Drain: wait (bounded) for every copy still in flight before exiting.
-        for (long long Q = base; Q < issued; ++Q) mbar_wait_bounded(&bars[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1));
+        for (long long Q = base; Q < issued; ++Q)
+            mbar_wait_bounded(&bars[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1));
     }
+}
+
+template <typename real, int W, int NSTAGE>
+__global__ void __launch_bounds__(W, 2) step_kernel(const __grid_constant__ StepArgs<real> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SingleWork<real, W> work{&A};
+    march<real, W, NSTAGE>(work, smem_raw, nullptr);
+}
+
+template <typename real, int W, int NSTAGE>
+__global__ void __launch_bounds__(W, 2) batch_step_kernel(const __grid_constant__ BatchArgs<real> B)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(16) StepArgs<real> sargs;
+    BatchWork<real, W> work{B.slots, B.items, *B.n_items, *B.T + B.s};
+    march<real, W, NSTAGE>(work, smem_raw, &sargs);
+}
+
+// Advance the batch's global step counter after a replay of k steps.
+static __global__ void batch_advance_kernel(long long *T, int k)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *T += k;
 }
 
 // ---------------------------------------------------------------------------

@@ -10,4 +10,10 @@ cudaError_t launch_totals(const double *partials, int nblocks, double *totals, c
     totals_kernel<<<1, 256, 0, s>>>(partials, nblocks, totals);
     return cudaGetLastError();
 }
+
+cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s)
+{
+    batch_advance_kernel<<<1, 32, 0, s>>>(T, k);
+    return cudaGetLastError();
+}
 }  // namespace dbm

@@ -18,6 +18,9 @@ struct KernelInfo {
 
 template <typename real> cudaError_t kernel_info(KernelInfo *out);
 template <typename real> cudaError_t launch_step(const StepArgs<real> &A, int grid, cudaStream_t s);
+template <typename real> cudaError_t batch_kernel_info(KernelInfo *out);
+template <typename real> cudaError_t launch_batch_step(const BatchArgs<real> &B, int grid, cudaStream_t s);
+cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const InitArgs<real> &A, cudaStream_t s);
 template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int grid, cudaStream_t s);
 cudaError_t launch_totals(const double *partials, int nblocks, double *totals, cudaStream_t s);

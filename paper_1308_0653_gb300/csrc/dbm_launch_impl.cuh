@@ -36,6 +36,30 @@ cudaError_t launch_step<DBM_REAL>(const StepArgs<DBM_REAL> &A, int grid, cudaStr
 }
 
 template <>
+cudaError_t batch_kernel_info<DBM_REAL>(KernelInfo *out)
+{
+    auto kern = batch_step_kernel<DBM_REAL, kW, kNS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW, kSmem);
+    if (e != cudaSuccess) return e;
+    out->W = kW;
+    out->nstage = kNS;
+    out->halo = kHalo;
+    out->smem = kSmem;
+    out->blocks_per_sm = nb;
+    return cudaSuccess;
+}
+
+template <>
+cudaError_t launch_batch_step<DBM_REAL>(const BatchArgs<DBM_REAL> &B, int grid, cudaStream_t s)
+{
+    batch_step_kernel<DBM_REAL, kW, kNS><<<grid, kW, kSmem, s>>>(B);
+    return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_init<DBM_REAL>(const InitArgs<DBM_REAL> &A, cudaStream_t s)
 {
     const long long n = (long long)A.nr * A.ntheta;

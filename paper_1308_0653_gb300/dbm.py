@@ -82,6 +82,21 @@ def lib():
         L.dbm_export_state.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.dbm_import_state.argtypes = [H, vp, vp, ctypes.c_int64, vp]
         L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 5
+        B = ctypes.c_void_p
+        L.dbm_batch_bytes.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int]
+        L.dbm_batch_bytes.restype = ctypes.c_size_t
+        L.dbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp,
+                                       ctypes.c_size_t, ctypes.POINTER(B)]
+        L.dbm_batch_destroy.argtypes = [B]
+        L.dbm_batch_attach.argtypes = [B, ctypes.c_int, H, ctypes.c_int64]
+        L.dbm_batch_detach.argtypes = [B, ctypes.c_int]
+        L.dbm_batch_remaining.argtypes = [B, ctypes.c_int]
+        L.dbm_batch_remaining.restype = ctypes.c_int64
+        L.dbm_batch_time.argtypes = [B]
+        L.dbm_batch_time.restype = ctypes.c_int64
+        L.dbm_batch_commit.argtypes = [B, vp]
+        L.dbm_batch_step.argtypes = [B, ctypes.c_int64, vp]
+        L.dbm_batch_launch_info.argtypes = [B] + [ctypes.POINTER(ctypes.c_int)] * 3
         _lib = L
     return _lib
 
@@ -203,6 +218,52 @@ def dbm_launch_info(h) -> dict:
                     [v.value for v in vals]))
 
 
+def dbm_batch_bytes(max_slots: int, max_items: int, precision: int) -> int:
+    return int(lib().dbm_batch_bytes(int(max_slots), int(max_items), int(precision)))
+
+
+def dbm_batch_create(max_slots, max_items, precision, rows_per_item, dev_ptr, nbytes):
+    b = ctypes.c_void_p()
+    _check(lib().dbm_batch_create(int(max_slots), int(max_items), int(precision), int(rows_per_item),
+                                  ctypes.c_void_p(dev_ptr), ctypes.c_size_t(nbytes), ctypes.byref(b)),
+           "dbm_batch_create")
+    return b
+
+
+def dbm_batch_destroy(b):
+    _check(lib().dbm_batch_destroy(b), "dbm_batch_destroy")
+
+
+def dbm_batch_attach(b, slot, h, nsteps):
+    _check(lib().dbm_batch_attach(b, int(slot), h, int(nsteps)), "dbm_batch_attach")
+
+
+def dbm_batch_detach(b, slot):
+    _check(lib().dbm_batch_detach(b, int(slot)), "dbm_batch_detach")
+
+
+def dbm_batch_remaining(b, slot) -> int:
+    return int(lib().dbm_batch_remaining(b, int(slot)))
+
+
+def dbm_batch_time(b) -> int:
+    return int(lib().dbm_batch_time(b))
+
+
+def dbm_batch_commit(b, stream=None):
+    _check(lib().dbm_batch_commit(b, _stream(stream)), "dbm_batch_commit")
+
+
+def dbm_batch_step(b, nsteps, stream=None):
+    _check(lib().dbm_batch_step(b, int(nsteps), _stream(stream)), "dbm_batch_step")
+
+
+def dbm_batch_launch_info(b) -> dict:
+    vals = [ctypes.c_int(0) for _ in range(3)]
+    _check(lib().dbm_batch_launch_info(b, *[ctypes.byref(v) for v in vals]), "dbm_batch_launch_info")
+    return dict(zip(("grid", "items", "rows_per_item"), [v.value for v in vals]))
+
+
 # ---- convenience ----------------------------------------------------------
 
 _PREC = {"fp32": DBM_FP32, "fp64": DBM_FP64, DBM_FP32: DBM_FP32, DBM_FP64: DBM_FP64}
@@ -284,6 +345,57 @@ class Simulation:
         if self.h is not None:
             dbm_destroy(self.h)
             self.h = None
+            self.buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch of simulations advanced together (device tables in a torch
+    buffer borrowed by the library)."""
+
+    def __init__(self, max_slots: int, max_items: int, precision="fp32", rows_per_item=0,
+                 device=None):
+        import torch
+        self.precision = _PREC[precision]
+        self.nbytes = dbm_batch_bytes(max_slots, max_items, self.precision)
+        if self.nbytes == 0:
+            raise DbmError(DBM_EINVAL, "dbm_batch_bytes")
+        dev = torch.device("cuda" if device is None else device)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=dev)
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.b = dbm_batch_create(max_slots, max_items, self.precision, rows_per_item, self.ptr,
+                                  self.nbytes)
+        self.sims = {}
+
+    def attach(self, slot: int, sim: "Simulation", nsteps: int):
+        dbm_batch_attach(self.b, slot, sim.h, nsteps)
+        self.sims[slot] = sim
+
+    def detach(self, slot: int):
+        dbm_batch_detach(self.b, slot)
+        self.sims.pop(slot, None)
+
+    def remaining(self, slot: int) -> int:
+        return dbm_batch_remaining(self.b, slot)
+
+    def time(self) -> int:
+        return dbm_batch_time(self.b)
+
+    def step(self, nsteps: int, stream=None):
+        dbm_batch_step(self.b, nsteps, stream)
+
+    def launch_info(self) -> dict:
+        return dbm_batch_launch_info(self.b)
+
+    def close(self):
+        if self.b is not None:
+            dbm_batch_destroy(self.b)
+            self.b = None
             self.buf = None
 
     def __del__(self):
