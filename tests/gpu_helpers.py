@@ -3,7 +3,8 @@ through the oracle, and compare fields by relative L-inf error.
 
 Relative L-inf of a field: max |gpu - oracle| / scale with scale = max |oracle|
 for rho, T and lambda (floored at 1e-12), and the largest oracle speed
-max(|u_r|, |u_theta|) for both velocity components (they vanish in places).
+max(|u_r|, |u_theta|) for both velocity components (they vanish in places),
+floored at 1e-3 of the thermal speed sqrt(max T) (a state at rest has u = 0).
 """
 import hashlib
 
@@ -18,7 +19,9 @@ TOL = {"fp64": 1e-11, "fp32": 1e-4}
 
 def rel_errors(gpu: dict, ref: dict) -> dict:
     out = {}
-    uscale = max(np.abs(ref["ur"]).max(), np.abs(ref["uth"]).max(), 1e-12)
+    # velocity floor: 1e-3 of the thermal speed (a state at rest has u = 0)
+    uscale = max(np.abs(ref["ur"]).max(), np.abs(ref["uth"]).max(),
+                 1e-3 * float(np.sqrt(np.abs(ref["T"]).max())))
     for k in FIELDS:
         if k in ("ur", "uth"):
             scale = uscale
