@@ -50,6 +50,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=40)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="step-kernel variant; 0 = autotune on a separate handle first")
+    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+                    help="step: the default line; batch: 64 uneven instances in one persistent "
+                         "launch per step; serve: Poisson arrivals through dbm_submit/dbm_poll")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--smax", type=int, default=20000)
+    ap.add_argument("--nmax", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -244,7 +255,16 @@ def run_ours(args):
     sites = w.sites
     stream = torch.cuda.Stream(device=dev)
 
-    sim = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
+    tune = None
+    if args.variant == 0:
+        # autotuner: time every kernel variant on a separate handle of the same
+        # size; the choice is remembered for this size class (used below)
+        t = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
+        t.init_state(w.fields, stream=stream)
+        best, ms = t.autotune(steps=20, stream=stream)
+        t.close()
+        tune = {"variant": best, "ms_per_step": {str(v + 1): round(x, 5) for v, x in enumerate(ms)}}
+    sim = dbm.Simulation(dict(w.params, precision="fp32", variant=args.variant), device=dev)
     sim.init_state(w.fields, stream=stream)
     sim.step(args.warmup, stream=stream)
     torch.cuda.synchronize(dev)
@@ -276,8 +296,10 @@ def run_ours(args):
     alg_bytes = BYTES_PER_SITE["fp32"] * sites
     achieved = alg_bytes / per_launch / 1e9
     peak, peak_src = measured_peak()
+    kname = {1: "dbm::step_kernel<float,128,6> (v1)", 2: "dbm::step_kernel_v2<float,128,6,false,2>",
+             3: "dbm::step_kernel_v2<float,128,4,true,3>"}.get(launch["variant"], f"variant {launch['variant']}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "dbm::step_kernel<float,128,6>",
+            "frac": achieved / peak, "traffic": None, "kernel": kname,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch * 1e3,
             "peak_source": peak_src}
     sim.close()
@@ -285,7 +307,7 @@ def run_ours(args):
     # FP64 path on the same workload (ALU-bound on GB300), for the FP32 vs FP64 ratio
     fp64 = None
     if args.fp64_steps > 0:
-        s64 = dbm.Simulation(dict(w.params, precision="fp64"), device=dev)
+        s64 = dbm.Simulation(dict(w.params, precision="fp64", variant=args.variant), device=dev)
         s64.init_state(w.fields, stream=stream)
         s64.step(4, stream=stream)
         torch.cuda.synchronize(dev)
@@ -295,7 +317,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         el64 = e0.elapsed_time(e1) / 1e3
         fp64 = {"value": sites * NV * args.fp64_steps / el64 / 1e9, "unit": UNIT,
-                "steps": args.fp64_steps, "kernel": "dbm::step_kernel<double,64,5>"}
+                "steps": args.fp64_steps, "variant": s64.launch_info()["variant"]}
         s64.close()
 
     # end to end through the C ABI with pinned host buffers: init from host,
@@ -307,7 +329,7 @@ def run_ours(args):
         outs = {k: torch.empty(w.fields[k].shape, dtype=torch.float64).pin_memory().numpy()
                 for k in dbm.FIELDS}
         tot = np.zeros(4)
-        sim = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
+        sim = dbm.Simulation(dict(w.params, precision="fp32", variant=args.variant), device=dev)
         sim.init_state(host_in, stream=stream)  # warm the path once
         sim.step(GRAPH_WARM, stream=stream)
         torch.cuda.synchronize(dev)
@@ -338,7 +360,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": elapsed_max / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_of(w, args, {"launch": launch}),
+                "config": config_of(w, args, {"launch": launch, "autotune": tune}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": args.steps, "fp64": fp64,
                 "fp32_over_fp64": (value / args.gpus / fp64["value"]) if fp64 else None,
@@ -352,10 +374,112 @@ def run_ours(args):
 GRAPH_WARM = 64
 
 
+def run_batch(args):
+    """64 uneven square instances (N in [128, 1024], seeded) advanced together,
+    one persistent launch per step, against the same instances run one by one."""
+    import torch
+    from paper_1308_0653_gb300 import dbm
+    torch.cuda.set_device(0)
+    ws = W.batch(args.instances, seed=0, nsteps=args.batch_steps, align=1)
+    sites = sum(w.sites for w in ws)
+    stream = torch.cuda.Stream()
+    sims = []
+    for w in ws:
+        s = dbm.Simulation(dict(w.params, precision="fp32"))
+        s.init_state(w.fields, stream=stream)
+        sims.append(s)
+    items = sum(((w.params["nr"] + 127) // 128) * ((w.params["ntheta"] + 15) // 16) for w in ws)
+    b = dbm.Batch(len(ws), items + 16, precision="fp32", rows_per_item=16)
+    for k, s in enumerate(sims):
+        b.attach(k, s, args.batch_steps)
+    b.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.batch_steps - args.warmup
+    e0.record(stream)
+    b.step(steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    batched = sites * NV * steps / el / 1e9
+    b.close()
+    # the same instances one at a time (a few steps each), for the ratio
+    t_one = 0.0
+    k1 = 64
+    for s in sims:
+        s.step(2, stream=stream)
+        e0.record(stream)
+        s.step(k1, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_one += e0.elapsed_time(e1) / 1e3 / k1
+    alone = sites * NV / t_one / 1e9
+    for s in sims:
+        s.close()
+    line = {"metric": METRIC + ", batched sweep", "value": batched, "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(ws)} instances, N x N with N uniform in [128, 1024] "
+                                   "(seed 0), explosion/implosion alternating, shock ratio "
+                                   "logU[1.2, 3], omega1 logU[0.5, 8]",
+                       "sites": sites, "work_items": items},
+            "one_by_one": {"value": alone, "unit": UNIT,
+                           "how": "each instance alone, 64 graph-replayed steps, summed time"},
+            "batched_over_one_by_one": batched / alone}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals through dbm_submit / dbm_poll: p50/p99 time to solution
+    of completed requests and aggregate GLUPS over the run."""
+    import torch
+    from paper_1308_0653_gb300 import dbm
+    torch.cuda.set_device(0)
+    free, total = torch.cuda.mem_get_info()
+    pool = int(min(free * 0.8, 150e9))
+    srv = dbm.Server(pool_bytes=pool, max_slots=64, max_queue=100000, quantum=64,
+                     max_items=1 << 20, rows_per_item=16)
+    arr = W.arrivals(args.rate, args.duration, seed=0)
+    t0 = time.perf_counter()
+    tickets = []
+    for k, ta in enumerate(arr):
+        w = W.serving_request(k, seed=0, nmax=args.nmax, smax=args.smax)
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.001)
+        tickets.append((srv.submit(dict(w.params, precision="fp32"), w.fields, w.nsteps), w))
+    lat, upd = [], 0.0
+    for t, w in tickets:
+        left = args.duration - (time.perf_counter() - t0)
+        st, res = srv.poll(t, timeout_us=int(max(left, 0) * 1e6))
+        if st == dbm.DBM_OK and res["status"] == dbm.DBM_OK:
+            lat.append(res["t_end"] - res["t_submit"])
+            upd += w.sites * NV * res["steps"]
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat) if lat else np.array([np.nan])
+    line = {"metric": METRIC + ", served", "value": upd / wall / 1e9, "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, side "
+                                   f"logU[128, {args.nmax}], steps logU[1000, {args.smax}], "
+                                   "explosion/implosion 50/50, omega1 in {1, 2, 4}",
+                       "requests": len(tickets), "pool_bytes": pool, "max_slots": 64, "quantum": 64},
+            "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.nanpercentile(lat, 50)),
+            "p99_s": float(np.nanpercentile(lat, 99)), "backlog": len(tickets) - int(np.isfinite(lat).sum()),
+            "server": stats}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

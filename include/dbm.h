@@ -78,7 +78,9 @@ typedef struct dbm_params {
     int32_t r_bc_inner;        /* DBM_BC_OUTFLOW                                  */
     int32_t r_bc_outer;        /* DBM_BC_OUTFLOW                                  */
     int32_t rows_per_item;     /* theta rows per CTA work item; 0 = automatic     */
-    int32_t reserved;          /* must be 0                                       */
+    int32_t variant;           /* step-kernel variant 1..dbm_num_variants();      */
+                               /* 0 = autotuned choice for the size class, else   */
+                               /* the library default                             */
     double r_in, r_out;        /* annulus radii, 0 < r_in < r_out (Sec. II.D)     */
     double dt, tau;            /* time step and BGK relaxation time (Sec. II.C)   */
     double Q;                  /* heat release per unit mass (Sec. II.A)          */
@@ -181,11 +183,28 @@ int dbm_export_state(dbm_t *h, void *f, void *lam, int64_t *steps, void *stream)
  * resuming is bitwise identical to an uninterrupted run.  Synchronises. */
 int dbm_import_state(dbm_t *h, const void *f, const void *lam, int64_t steps, void *stream);
 
-/* Launch shape chosen at create time (any pointer may be NULL): persistent
- * CTAs in the grid, threads (radial sites) per CTA, dynamic shared memory per
- * CTA, theta rows per work item and the number of work items per step. */
+/* Launch shape of the handle (any pointer may be NULL): persistent CTAs in
+ * the grid, threads per CTA, dynamic shared memory per CTA, theta rows per
+ * work item, work items per step and the step-kernel variant. */
 int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes,
-                    int *rows_per_item, int *items);
+                    int *rows_per_item, int *items, int *variant);
+
+/* Number of step-kernel variants for a precision (0 if invalid).  Variants
+ * differ only in how the work is staged (pipeline, ring depth, registers);
+ * every variant computes the same update bit for bit. */
+int dbm_num_variants(int precision);
+
+/* Switch the handle to step-kernel variant 1..dbm_num_variants(). */
+int dbm_set_variant(dbm_t *h, int variant);
+
+/* Autotuner: time every variant on the handle's own state for `steps`
+ * launches each (after 2 untimed ones) with CUDA events on `stream`, switch
+ * the handle to the fastest and remember it for the handle's size class
+ * (precision x ceil(log2 nr) x ceil(log2 ntheta)), which dbm_create then uses
+ * for params with variant 0 for the rest of the process.  The timing steps
+ * advance the simulation (num_variants x (steps + 2) steps).  *best receives
+ * the chosen variant, ms_per_step[v-1] (may be NULL) each variant's time. */
+int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_step);
 
 /* ---- batches: many uneven simulations, one persistent launch per step ---- */
 /*
@@ -244,6 +263,91 @@ int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
 
 /* Launch shape: persistent grid, current number of work items, rows per item. */
 int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item);
+
+/* ---- serving: continuous batching behind submit / poll ------------------ */
+/*
+ * A server owns a batch and a scheduler thread.  dbm_submit queues a request
+ * (parameters, host initial fields, number of steps); the scheduler admits
+ * queued requests into free batch slots as soon as its device pool has room
+ * (first fit in arrival order; a request passed over max_bypass times blocks
+ * later ones until it starts), advances all resident simulations quantum by
+ * quantum in shared launches, and retires finished ones: their moments go to
+ * host memory and dbm_poll hands them out.  Per-request upload and download
+ * run on a second stream and overlap the batched steps.  Each result equals
+ * the result of running the request alone (same kernel, same bits).
+ */
+typedef struct dbm_server_s dbm_server_t;
+
+typedef struct dbm_server_config {
+    int32_t max_slots;      /* simulations resident at once (batch slots)          */
+    int32_t max_queue;      /* queued requests beyond which dbm_submit is EBUSY    */
+    int32_t quantum;        /* steps per scheduling round (32 | quantum: graphs)   */
+    int32_t precision;      /* DBM_FP32 or DBM_FP64, shared by all requests        */
+    int64_t max_items;      /* capacity of the batch's work-item table             */
+    int32_t rows_per_item;  /* theta rows per work item (0 = 16)                   */
+    int32_t max_bypass;     /* how often a queued request may be passed over       */
+} dbm_server_config;
+
+typedef struct dbm_fields {  /* host arrays [ntheta][nr], read during dbm_submit */
+    const double *rho, *ur, *uth, *T, *lam;
+} dbm_fields;
+
+typedef struct dbm_result {
+    int32_t status;          /* DBM_OK, DBM_ECANCELLED, DBM_ENONFINITE, ...        */
+    int32_t nr, ntheta;
+    int32_t pad;
+    int64_t steps;           /* steps taken                                       */
+    double *rho, *ur, *uth, *T, *lam; /* library-owned host arrays [ntheta][nr]   */
+                                      /* (NULL unless status is OK or ENONFINITE) */
+    double totals[4];        /* as dbm_moments                                    */
+    double t_submit, t_start, t_end;  /* seconds on the server's clock            */
+} dbm_result;
+
+typedef struct dbm_server_stats {
+    double submitted, completed, failed, cancelled;
+    double queued, running;
+    double updates;            /* site x velocity updates of completed requests  */
+    double pool_free_largest;  /* bytes                                           */
+    double batch_time;         /* steps of the batch clock                        */
+    int32_t status;            /* first error of the batched steps, or DBM_OK     */
+    int32_t pad;
+} dbm_server_stats;
+
+/* Host-only: device bytes the server itself needs inside its pool (the batch
+ * tables); the rest of the pool holds the resident simulations. */
+size_t dbm_server_min_bytes(const dbm_server_config *cfg);
+
+/* Start a server on caller device memory (256-byte aligned), on the current
+ * device.  The caller keeps ownership of dev_pool until dbm_server_destroy.
+ * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
+int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_bytes,
+                      dbm_server_t **out);
+
+/* Queue a simulation: params (precision must match the server's), initial
+ * fields (copied before return), nsteps.  *ticket identifies it.
+ * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (larger than the whole pool),
+ * DBM_EBUSY (queue full). */
+int dbm_submit(dbm_server_t *s, const dbm_params *p, const dbm_fields *init, int64_t nsteps,
+               uint64_t *ticket);
+
+/* Wait up to timeout_us (0: do not wait, < 0: forever) for a request.  On
+ * DBM_OK *out holds its result (status inside) and the ticket is consumed;
+ * free the arrays with dbm_result_free.  DBM_ENOTREADY (timeout_us = 0 and
+ * still queued or running), DBM_ETIMEOUT, DBM_ENOTFOUND. */
+int dbm_poll(dbm_server_t *s, uint64_t ticket, dbm_result *out, int64_t timeout_us);
+
+/* Free the host arrays of a polled result. */
+int dbm_result_free(dbm_result *res);
+
+/* Cancel a queued or running request (its result status becomes
+ * DBM_ECANCELLED; a running one leaves the batch at the next quantum). */
+int dbm_cancel(dbm_server_t *s, uint64_t ticket);
+
+/* Counters of the server. */
+int dbm_server_stats_get(dbm_server_t *s, dbm_server_stats *out);
+
+/* Cancel what is left, stop the scheduler, free everything but dev_pool. */
+int dbm_server_destroy(dbm_server_t *s);
 
 #ifdef __cplusplus
 }

@@ -8,6 +8,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -124,6 +126,7 @@ struct dbm_s {
     int cur;
     int64_t steps;
     KernelInfo ki;
+    int variant;              // kernel variant (1..num_variants)
     int grid, rows_per_item, items;
     StepArgs<float> a32[2];   // [0]: f0 -> f1, [1]: f1 -> f0
     StepArgs<double> a64[2];
@@ -215,8 +218,8 @@ int upload_tables(dbm_t *h)
 
 int launch_one(dbm_t *h, int b, cudaStream_t s)
 {
-    cudaError_t e = h->p.precision == DBM_FP64 ? launch_step<double>(h->a64[b], h->grid, s)
-                                               : launch_step<float>(h->a32[b], h->grid, s);
+    cudaError_t e = h->p.precision == DBM_FP64 ? launch_step<double>(h->variant, h->a64[b], h->grid, s)
+                                               : launch_step<float>(h->variant, h->a32[b], h->grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
     return DBM_OK;
 }
@@ -239,6 +242,70 @@ int build_graph(dbm_t *h)
     if (e != cudaSuccess) {
         h->graph = nullptr;
         return cuda_fail(e, "step graph capture");
+    }
+    return DBM_OK;
+}
+
+// Size classes of the autotuner: precision x ceil(log2 nr) x ceil(log2 ntheta).
+std::mutex g_tune_mu;
+std::map<long long, int> g_tuned;
+
+long long size_class(const dbm_params &p)
+{
+    auto lg = [](int x) {
+        int l = 0;
+        while ((1LL << l) < x) ++l;
+        return l;
+    };
+    return ((long long)p.precision << 16) | ((long long)lg(p.nr) << 8) | lg(p.ntheta);
+}
+
+int pick_variant(const dbm_params &p)
+{
+    if (p.variant > 0) return p.variant;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(size_class(p));
+        if (it != g_tuned.end()) return it->second;
+    }
+    return p.precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
+}
+
+// Launch shape for a kernel variant: persistent CTAs, one per resident slot;
+// theta rows per item chosen so the items fill the slots in one wave.
+int configure_launch(dbm_t *h, int variant)
+{
+    KernelInfo ki;
+    cudaError_t e = h->p.precision == DBM_FP64 ? kernel_info<double>(variant, &ki)
+                                               : kernel_info<float>(variant, &ki);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel variant query");
+    if (ki.blocks_per_sm < 1) {
+        snprintf(g_last_error, sizeof(g_last_error), "step kernel variant %d does not fit on an SM", variant);
+        return DBM_ECUDA;
+    }
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const dbm_params &p = h->p;
+    const int slots = nsm * ki.blocks_per_sm;
+    const int strips = (p.nr + ki.W - 1) / ki.W;
+    int L_rows = p.rows_per_item;
+    if (L_rows == 0) {
+        const long long need = ((long long)p.ntheta * strips + slots - 1) / slots;
+        L_rows = (int)std::max(1LL, need);
+    }
+    L_rows = std::min(L_rows, p.ntheta);
+    h->ki = ki;
+    h->variant = variant;
+    h->rows_per_item = L_rows;
+    h->items = strips * ((p.ntheta + L_rows - 1) / L_rows);
+    h->grid = std::min(h->items, slots);
+    if (p.precision == DBM_FP64)
+        fill_step_args<double>(h, h->a64);
+    else
+        fill_step_args<float>(h, h->a32);
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
     }
     return DBM_OK;
 }
@@ -302,7 +369,9 @@ int dbm_check(const dbm_params *p, double *cfl)
     if (p->precision != DBM_FP32 && p->precision != DBM_FP64) return DBM_EINVAL;
     if (p->reaction_energy != DBM_R_EXPLICIT && p->reaction_energy != DBM_R_CONSISTENT) return DBM_EINVAL;
     if (p->r_bc_inner != DBM_BC_OUTFLOW || p->r_bc_outer != DBM_BC_OUTFLOW) return DBM_EINVAL;
-    if (p->rows_per_item < 0 || p->reserved != 0) return DBM_EINVAL;
+    if (p->rows_per_item < 0 || p->variant < 0) return DBM_EINVAL;
+    if (p->variant > (p->precision == DBM_FP64 ? num_variants<double>() : num_variants<float>()))
+        return DBM_EINVAL;
     if (!finite_pos(p->r_in) || !std::isfinite(p->r_out) || p->r_out <= p->r_in) return DBM_EINVAL;
     if (!finite_pos(p->dt) || !(p->tau > 0.0)) return DBM_EINVAL;  // tau may be +inf-like large
     if (!std::isfinite(p->Q) || !std::isfinite(p->T_th)) return DBM_EINVAL;
@@ -362,33 +431,15 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
     h->ld = padded_ld(p->nr);
     h->plane = (long long)h->ld * p->ntheta;
     cudaError_t e = cudaGetDevice(&h->device);
-    if (e == cudaSuccess)
-        e = p->precision == DBM_FP64 ? kernel_info<double>(&h->ki) : kernel_info<float>(&h->ki);
-    int nsm = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) {
         delete h;
         return cuda_fail(e, "dbm_create: device query");
     }
-    if (h->ki.blocks_per_sm < 1) {
+    rc = configure_launch(h, pick_variant(*p));
+    if (rc != DBM_OK) {
         delete h;
-        snprintf(g_last_error, sizeof(g_last_error), "step kernel does not fit on an SM");
-        return DBM_ECUDA;
+        return rc;
     }
-    // Launch shape: persistent CTAs, one per resident slot; theta rows per
-    // item chosen so the items fill the slots in one wave.
-    const int slots = nsm * h->ki.blocks_per_sm;
-    const int strips = (p->nr + h->ki.W - 1) / h->ki.W;
-    int L_rows = p->rows_per_item;
-    if (L_rows == 0) {
-        const long long need = ((long long)p->ntheta * strips + slots - 1) / slots;
-        L_rows = (int)std::max(1LL, need);
-    }
-    L_rows = std::min(L_rows, p->ntheta);
-    h->rows_per_item = L_rows;
-    h->items = strips * ((p->ntheta + L_rows - 1) / L_rows);
-    h->grid = std::min(h->items, slots);
-
     e = cudaMemset(dev_buf, 0, L.total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -400,10 +451,6 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
         delete h;
         return rc;
     }
-    if (p->precision == DBM_FP64)
-        fill_step_args<double>(h, h->a64);
-    else
-        fill_step_args<float>(h, h->a32);
     *out = h;
     return DBM_OK;
 }
@@ -625,14 +672,83 @@ int dbm_import_state(dbm_t *h, const void *f, const void *lam, int64_t steps, vo
 }
 
 int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes, int *rows_per_item,
-                    int *items)
+                    int *items, int *variant)
 {
     if (!h) return DBM_EINVAL;
     if (grid) *grid = h->grid;
-    if (threads) *threads = h->ki.W;
+    if (variant) *variant = h->variant;
+    if (threads) *threads = h->ki.threads;
     if (smem_bytes) *smem_bytes = h->ki.smem;
     if (rows_per_item) *rows_per_item = h->rows_per_item;
     if (items) *items = h->items;
+    return DBM_OK;
+}
+
+int dbm_num_variants(int precision)
+{
+    if (precision == DBM_FP32) return num_variants<float>();
+    if (precision == DBM_FP64) return num_variants<double>();
+    return 0;
+}
+
+int dbm_set_variant(dbm_t *h, int variant)
+{
+    if (!h || variant < 1 || variant > dbm_num_variants(h->p.precision)) return DBM_EINVAL;
+    return configure_launch(h, variant);
+}
+
+int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_step)
+{
+    if (!h || steps < 1) return DBM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nv = dbm_num_variants(h->p.precision);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int bestv = 0;
+    float bestms = 0.f;
+    int rc = DBM_OK;
+    for (int v = 1; v <= nv && rc == DBM_OK; ++v) {
+        rc = configure_launch(h, v);
+        if (rc != DBM_OK) break;
+        // two untimed steps, then `steps` timed single launches
+        for (int k = 0; k < 2 && rc == DBM_OK; ++k) {
+            rc = launch_one(h, h->cur, s);
+            h->cur ^= 1;
+            h->steps += 1;
+        }
+        if (rc != DBM_OK) break;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < steps && rc == DBM_OK; ++k) {
+            rc = launch_one(h, h->cur, s);
+            h->cur ^= 1;
+            h->steps += 1;
+        }
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= steps;
+        if (ms_per_step) ms_per_step[v - 1] = ms;
+        if (bestv == 0 || ms < bestms) {
+            bestv = v;
+            bestms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DBM_OK) return rc;
+    rc = configure_launch(h, bestv);
+    if (rc != DBM_OK) return rc;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[size_class(h->p)] = bestv;
+    }
+    if (best) *best = bestv;
     return DBM_OK;
 }
 
@@ -660,6 +776,7 @@ struct dbm_batch_s {
     int n_items;
     bool dirty;
     KernelInfo ki;
+    int variant;
     int grid;
     cudaGraphExec_t graph;    // GRAPH_STEPS batch steps + counter advance
 };
@@ -718,13 +835,13 @@ int batch_launch(dbm_batch_t *b, int s, cudaStream_t st)
                             reinterpret_cast<const int4 *>(b->buf + b->off_items),
                             reinterpret_cast<const int *>(b->buf + b->off_nitems),
                             reinterpret_cast<const long long *>(b->buf + b->off_T), s};
-        e = launch_batch_step<double>(B, b->grid, st);
+        e = launch_batch_step<double>(b->variant, B, b->grid, st);
     } else {
         BatchArgs<float> B{reinterpret_cast<const BatchSlot<float> *>(b->buf + b->off_slots),
                            reinterpret_cast<const int4 *>(b->buf + b->off_items),
                            reinterpret_cast<const int *>(b->buf + b->off_nitems),
                            reinterpret_cast<const long long *>(b->buf + b->off_T), s};
-        e = launch_batch_step<float>(B, b->grid, st);
+        e = launch_batch_step<float>(b->variant, B, b->grid, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "batch step kernel launch");
     return DBM_OK;
@@ -812,8 +929,10 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b->variant = precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
     if (e == cudaSuccess)
-        e = precision == DBM_FP64 ? batch_kernel_info<double>(&b->ki) : batch_kernel_info<float>(&b->ki);
+        e = precision == DBM_FP64 ? batch_kernel_info<double>(b->variant, &b->ki)
+                                  : batch_kernel_info<float>(b->variant, &b->ki);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->stage, L.items + (size_t)max_items * sizeof(int4) + 256,
                                             cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev, cudaEventDisableTiming);

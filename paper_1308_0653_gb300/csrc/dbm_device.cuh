@@ -116,6 +116,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Barrier over the first `nthreads` threads only (id 1; id 0 is __syncthreads).
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -136,19 +147,43 @@ template <> __device__ __forceinline__ float pow_<float>(float x, float y) { ret
 template <> __device__ __forceinline__ double pow_<double>(double x, double y) { return pow(x, y); }
 
 // ---------------------------------------------------------------------------
+// Explicitly rounded arithmetic.  Every operation of the site update is an
+// IEEE round-to-nearest intrinsic (no contraction, no reassociation), so the
+// update is the same bit pattern in every kernel variant, in batched and
+// single launches, and in graph replays.
+// ---------------------------------------------------------------------------
+template <typename real> struct Op;
+template <> struct Op<float> {
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+};
+template <> struct Op<double> {
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+
+// ---------------------------------------------------------------------------
 // One site's update (Eq. LB_evolution_equation, Eq. Eqlambda), all 33
 // velocities unrolled.  sp/sc/sn: shared-memory buffers of rows m-1, m, m+1;
 // col = HALO + tx.  Velocity (k, i) has Cartesian direction i pi / 4, so its
 // moments and equilibrium use the fixed direction cosines; its polar Courant
 // numbers use the row's c_i = cos(i pi/4 - theta_m), s_i = sin(...).
 // ---------------------------------------------------------------------------
-template <typename real, int WP>
+template <typename real, int WP, bool REREAD = false>
 __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real *__restrict__ sp,
                                             const real *__restrict__ sc,
                                             const real *__restrict__ sn, int col, int j, int m,
                                             real inv_r, const real (&cs)[8], const real (&sn8)[8])
 {
+    using O = Op<real>;
     const real H = real(0.70710678118654752440);  // cos(pi/4)
+    const real one = real(1), half = real(0.5);
 
     // --- a1: load the site's 33 f and lambda -------------------------------
     real f[NV];
@@ -157,81 +192,85 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     const real lam = sc[NV * WP + col];
 
     // --- a2: moments, ring by ring (Cartesian components) ------------------
+    //     rho = sum f, rho u = sum f v, e2 = sum f v^2, T = (e2/rho - u^2)/2
     real rho = f[0], jx = real(0), jy = real(0), e2 = real(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const real *g = &f[1 + 8 * k];
-        const real s0 = ((g[0] + g[4]) + (g[2] + g[6])) + ((g[1] + g[5]) + (g[3] + g[7]));
-        const real a = g[1] - g[5], b = g[3] - g[7];
-        const real sx = (g[0] - g[4]) + H * (a - b);
-        const real sy = (g[2] - g[6]) + H * (a + b);
-        rho += s0;
-        jx += A.v[k] * sx;
-        jy += A.v[k] * sy;
-        e2 += A.v2[k] * s0;
+        const real s0 = O::add(O::add(O::add(g[0], g[4]), O::add(g[2], g[6])),
+                               O::add(O::add(g[1], g[5]), O::add(g[3], g[7])));
+        const real a = O::sub(g[1], g[5]), b = O::sub(g[3], g[7]);
+        const real sx = O::fma(H, O::sub(a, b), O::sub(g[0], g[4]));
+        const real sy = O::fma(H, O::add(a, b), O::sub(g[2], g[6]));
+        rho = O::add(rho, s0);
+        jx = O::fma(A.v[k], sx, jx);
+        jy = O::fma(A.v[k], sy, jy);
+        e2 = O::fma(A.v2[k], s0, e2);
     }
-    const real inv_rho = rcp_(rho);
-    const real ux = jx * inv_rho, uy = jy * inv_rho;
-    const real u2 = ux * ux + uy * uy;
-    const real T = real(0.5) * (e2 * inv_rho - u2);
-    const real inv_T = rcp_(T);
+    const real inv_rho = O::div(one, rho);
+    const real ux = O::mul(jx, inv_rho), uy = O::mul(jy, inv_rho);
+    const real u2 = O::fma(ux, ux, O::mul(uy, uy));
+    const real T = O::mul(half, O::sub(O::mul(e2, inv_rho), u2));
+    const real inv_T = O::div(one, T);
 
     // --- a3: weights F_k(T), F_0 = 1 - 8 sum F_k ---------------------------
     real F[4];
     real Fsum = real(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        F[k] = T * (A.Fc[k][0] + T * (A.Fc[k][1] + T * (A.Fc[k][2] + T * A.Fc[k][3])));
-        Fsum += F[k];
+        F[k] = O::mul(T, O::fma(T, O::fma(T, O::fma(T, A.Fc[k][3], A.Fc[k][2]), A.Fc[k][1]), A.Fc[k][0]));
+        Fsum = O::add(Fsum, F[k]);
     }
-    const real F0 = real(1) - real(8) * Fsum;
+    const real F0 = O::fma(real(-8), Fsum, one);
 
     // --- a4 coefficients: f^eq = rho F_k [A0 + A1 xi + A2 xi^2 + xi^3/6 + xi^4/24],
     //     xi = v.u / T ---------------------------------------------------------
-    const real hh = real(0.5) * u2 * inv_T;
-    const real A0 = real(1) - hh + real(0.5) * hh * hh;
-    const real A1 = real(1) - hh;
-    const real A2 = real(0.5) * A1;
-    const real wx = ux * inv_T, wy = uy * inv_T;
+    const real hh = O::mul(O::mul(half, u2), inv_T);
+    const real A1 = O::sub(one, hh);
+    const real A0 = O::fma(O::mul(half, hh), hh, A1);
+    const real A2 = O::mul(half, A1);
+    const real wx = O::mul(ux, inv_T), wy = O::mul(uy, inv_T);
     real w[8];
     w[0] = wx;
     w[2] = wy;
-    w[1] = H * (wx + wy);
-    w[3] = H * (wy - wx);
+    w[1] = O::mul(H, O::add(wx, wy));
+    w[3] = O::mul(H, O::sub(wy, wx));
     w[4] = -w[0];
     w[5] = -w[1];
     w[6] = -w[2];
     w[7] = -w[3];
 
     // --- a5: Cochran rate with ignition gate; exact lambda step (a9) -------
-    const real P = rho * T;
+    const real P = O::mul(rho, T);
     real a = real(0), b = real(0);
     if (T > A.T_th) {
         if (A.general_pow) {
-            a = A.omega1 * pow_(P, A.m_exp);
-            b = A.omega2 * pow_(P, A.n_exp);
+            a = O::mul(A.omega1, pow_(P, A.m_exp));
+            b = O::mul(A.omega2, pow_(P, A.n_exp));
         } else {
-            a = A.omega1 * P;
-            b = A.omega2 * P;
+            a = O::mul(A.omega1, P);
+            b = O::mul(A.omega2, P);
         }
     }
-    const real om = real(1) - lam;
-    const real g = a + b * lam;
-    real R = om * g;
-    const real sab = a + b;
+    const real om = O::sub(one, lam);
+    const real g = O::fma(b, lam, a);  // a + b lam
+    real R = O::mul(om, g);
+    const real sab = O::add(a, b);
     real dlam = real(0);
     if (sab > real(0)) {
-        const real em1 = expm1_(sab * A.dt);
-        dlam = om * g * em1 / (sab + g * em1);
+        // lam+ - lam = (1-lam)(a+b lam)(E-1) / [(a+b) + (a+b lam)(E-1)], E = e^{(a+b)dt}
+        const real em1 = expm1_(O::mul(sab, A.dt));
+        dlam = O::div(O::mul(O::mul(om, g), em1), O::fma(g, em1, sab));
     }
-    if (A.reaction_energy) R = dlam / A.dt;
+    if (A.reaction_energy) R = O::div(dlam, A.dt);
 
     // --- a6+a7 coefficients: f_new = poly(xi) (beta_k - gamma_k xi) + ... ---
     //     M = f^eq ((v-u)^2 - 2T) / (2T^2) Q R with (v-u)^2 = v_k^2 + u^2 - 2 T xi
-    const real QR = A.Q * R;
-    const real half_inv_T2 = real(0.5) * inv_T * inv_T;
-    const real gam = A.dt * QR * inv_T;
-    const real beta0 = rho * F0 * (A.one_m_decay + A.dt * QR * (u2 - real(2) * T) * half_inv_T2);
+    const real dtQR = O::mul(A.dt, O::mul(A.Q, R));
+    const real half_inv_T2 = O::mul(O::mul(half, inv_T), inv_T);
+    const real gam = O::mul(dtQR, inv_T);
+    const real u2m2T = O::fma(real(-2), T, u2);
+    const real beta0 = O::mul(O::mul(rho, F0), O::fma(O::mul(dtQR, u2m2T), half_inv_T2, A.one_m_decay));
 
     // --- a8: per-direction Courant magnitudes and upwind neighbours --------
     real ar[8], at[8], sa[8];
@@ -239,9 +278,9 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     const int to_prev = (int)(sp - sc), to_next = (int)(sn - sc);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        ar[i] = fabs(cs[i]) * A.cr_scale;
-        at[i] = fabs(sn8[i]) * A.ct_scale * inv_r;
-        sa[i] = ar[i] + at[i];
+        ar[i] = O::mul(fabs(cs[i]), A.cr_scale);
+        at[i] = O::mul(O::mul(fabs(sn8[i]), A.ct_scale), inv_r);
+        sa[i] = O::add(ar[i], at[i]);
         int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
         if ((j == 0 && o < 0) || (j == A.nr - 1 && o > 0)) o = 0;  // zero-gradient ghost
         rn[i] = col + o;
@@ -249,37 +288,43 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     }
 
     // --- a7 + a11: update all velocities and store ------------------------
+    //     f_new = f^eq (1 - E + dt M/f^eq) + (E - |C_r| - |C_th|) f
+    //             + |C_r| f(upwind r) + |C_th| f(upwind theta)
     real *out = A.f_out + (long long)m * A.ld + j;
-    out[0] = A0 * beta0 + A.decay * f[0];
+    out[0] = O::fma(A0, beta0, O::mul(A.decay, REREAD ? sc[col] : f[0]));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const real vk = A.v[k];
-        const real rF = rho * F[k];
-        const real beta = rF * (A.one_m_decay + A.dt * QR * (A.v2[k] + u2 - real(2) * T) * half_inv_T2);
-        const real gamma = rF * gam;
+        const real rF = O::mul(rho, F[k]);
+        const real beta = O::mul(rF, O::fma(O::mul(dtQR, O::add(A.v2[k], u2m2T)), half_inv_T2, A.one_m_decay));
+        const real gamma = O::mul(rF, gam);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int q = 1 + 8 * k + i;
-            const real xi = vk * w[i];
-            const real poly = A0 + xi * (A1 + xi * (A2 + xi * (real(1.0 / 6.0) + xi * real(1.0 / 24.0))));
-            real t = poly * (beta - gamma * xi);
-            t += (A.decay - vk * sa[i]) * f[q];
-            const real adv = ar[i] * sc[q * WP + rn[i]] + at[i] * sc[q * WP + tn[i]];
-            t += vk * adv;
+            const real xi = O::mul(vk, w[i]);
+            const real poly = O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0);
+            real t = O::mul(poly, O::fma(-gamma, xi, beta));
+            // REREAD: take f from shared memory again instead of holding all
+            // 33 values in registers across the moment pass (fewer registers)
+            const real fq = REREAD ? sc[q * WP + col] : f[q];
+            t = O::fma(O::fma(-vk, sa[i], A.decay), fq, t);
+            const real adv = O::fma(ar[i], sc[q * WP + rn[i]], O::mul(at[i], sc[q * WP + tn[i]]));
+            t = O::fma(vk, adv, t);
             out[(long long)q * A.plane] = t;
         }
     }
 
     // --- a9 + a10: lambda = exact reaction step + upwind transport ---------
     const real cth = cs[0], sth = -sn8[0];  // cos(theta_m), sin(theta_m)
-    const real ur = ux * cth + uy * sth;
-    const real uth = -ux * sth + uy * cth;
+    const real ur = O::fma(ux, cth, O::mul(uy, sth));
+    const real uth = O::fma(uy, cth, -O::mul(ux, sth));
     int orr = ur >= real(0) ? -1 : 1;
     if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
     const real lr = sc[NV * WP + col + orr];
     const real lt = (uth >= real(0) ? sp : sn)[NV * WP + col];
-    real ln = lam + dlam - fabs(ur) * A.cr_scale * (lam - lr) -
-              fabs(uth) * A.ct_scale * inv_r * (lam - lt);
+    real ln = O::add(lam, dlam);
+    ln = O::sub(ln, O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lam, lr)));
+    ln = O::sub(ln, O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lam, lt)));
     ln = fmin(fmax(ln, real(0)), real(1));
     A.lam_out[(long long)m * A.ld + j] = ln;
 }
@@ -514,6 +559,199 @@ __global__ void __launch_bounds__(W, 2) batch_step_kernel(const __grid_constant_
 static __global__ void batch_advance_kernel(long long *T, int k)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *T += k;
+}
+
+// ---------------------------------------------------------------------------
+// v2 pipeline: warp-specialised.  Warp W/32 is the producer: it issues the
+// TMA bulk copies of each row (34 arrays + the row's 16 trig values) into a
+// ring of NSTAGE buffers.  The W/32 consumer warps each update 32 sites of the
+// row.  Per buffer, a "full" mbarrier (count 1 + transaction bytes) tells the
+// consumers a row has landed, and an "empty" mbarrier (count = consumer warps)
+// tells the producer every consumer warp is done with it.  There is no
+// CTA-wide barrier per row, so warps drift within the ring instead of waiting
+// for the slowest.  Positions are released after their last use: after
+// centre P the buffer of P-1, and at an item's last centre also P and P+1.
+// ---------------------------------------------------------------------------
+template <typename real, int W, int NSTAGE, bool REREAD, typename Work>
+__device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw,
+                                       StepArgs<real> *sargs2)
+{
+    constexpr int HALO = Halo<real>::value;
+    constexpr int WP = W + 2 * HALO;
+    constexpr int TAB = 16;
+    constexpr int SLOT = NARR * WP + TAB;  // elements per row buffer (trig values last)
+    constexpr int NCW = W / 32;            // consumer warps
+    static_assert(NSTAGE >= 3, "rows m-1, m, m+1 must be resident");
+    static_assert((SLOT * sizeof(real)) % 16 == 0, "row buffers must stay 16-byte aligned");
+
+    real *sm = reinterpret_cast<real *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + sizeof(real) * NSTAGE * SLOT);
+    uint64_t *empty = full + NSTAGE;
+    __shared__ int abort_flag;
+    __shared__ long long issued_total;
+
+    const int tx = threadIdx.x;
+    const int warp = tx >> 5, lane = tx & 31;
+    const int nitems = work.count();
+
+    if (tx == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_mbar_init();
+        abort_flag = 0;
+        issued_total = 0;
+    }
+    __syncthreads();
+
+    if (warp == NCW) {
+        // ------------------------------ producer ------------------------------
+        long long total_loads = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const StepArgs<real> *a;
+            int j0, mb, me;
+            if (work.item(it, a, j0, mb, me)) total_loads += (me - mb) + 2;
+        }
+        long long issued = 0;
+        int p_item = blockIdx.x, p_row = 0;
+        const StepArgs<real> *pa = nullptr;
+        int pj0 = 0, pmb = 0, pme = 0;
+        bool p_ok = false;
+        while (issued < total_loads) {
+            const int slot = (int)(issued % NSTAGE);
+            while (!p_ok) {
+                p_ok = work.item(p_item, pa, pj0, pmb, pme);
+                if (!p_ok) p_item += gridDim.x;
+            }
+            if (issued >= NSTAGE) {
+                const uint32_t par = (uint32_t)(((issued / NSTAGE) - 1) & 1);
+                if (!mbar_wait_bounded(&empty[slot], par)) {
+                    if (lane == 0) atomicOr(pa->status, ST_WAIT_TIMEOUT);
+                    abort_flag = 1;
+                }
+            }
+            __syncwarp();
+            if (*(volatile int *)&abort_flag) break;
+            int m = pmb - 1 + p_row;
+            const int nth = pa->ntheta;
+            m = m < 0 ? m + nth : (m >= nth ? m - nth : m);
+            const int jlo = max(pj0 - HALO, 0);
+            const int jhi = min(pj0 + W + HALO, pa->ld);
+            const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
+            real *buf = sm + slot * SLOT;
+            real *dst = buf + (jlo - (pj0 - HALO));
+            if (lane == 0) mbar_arrive_expect_tx(&full[slot], nbytes * NARR + TAB * (uint32_t)sizeof(real));
+            __syncwarp();
+            fence_proxy_async_smem();
+            const long long roff = (long long)m * pa->ld + jlo;
+            for (int a = lane; a < NARR; a += 32) {
+                const real *src = (a < NV) ? pa->f_in + (long long)a * pa->plane + roff : pa->lam_in + roff;
+                bulk_g2s(dst + a * WP, src, nbytes, &full[slot]);
+            }
+            if (lane == 31) bulk_g2s(buf + NARR * WP, pa->rowtab + (long long)m * TAB, TAB * sizeof(real), &full[slot]);
+            ++issued;
+            if (++p_row == (pme - pmb) + 2) {
+                p_row = 0;
+                p_item += gridDim.x;
+                p_ok = false;
+            }
+        }
+        if (lane == 0) issued_total = issued;
+    } else {
+        // ------------------------------ consumers -----------------------------
+        long long base = 0;
+        int parity = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+            const StepArgs<real> *ga;
+            int j0, mb, me;
+            if (!work.item(it, ga, j0, mb, me)) continue;
+            const StepArgs<real> *ap = ga;
+            if constexpr (Work::kCopyArgs) {
+                // per-instance constants into shared memory, double-buffered:
+                // the barrier of the previous item guarantees nobody still
+                // reads the copy made two items ago
+                StepArgs<real> *dst = sargs2 + parity;
+                const int nw = (int)(sizeof(StepArgs<real>) / sizeof(int));
+                for (int q = tx; q < nw; q += W)
+                    reinterpret_cast<int *>(dst)[q] = reinterpret_cast<const int *>(ga)[q];
+                named_bar_sync(1, W);
+                ap = dst;
+                parity ^= 1;
+            }
+            const StepArgs<real> &A = *ap;
+            const int L = me - mb;
+            const int j = j0 + tx;
+            const bool active = j < A.nr;
+            const real inv_r = A.inv_r[active ? j : 0];
+            for (int c = 1; c <= L; ++c) {
+                const long long P = base + c;
+                for (long long Q = (c == 1 ? P - 1 : P + 1); Q <= P + 1; ++Q) {
+                    if (!mbar_wait_bounded(&full[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1))) {
+                        if (lane == 0) atomicOr(A.status, ST_WAIT_TIMEOUT);
+                        abort_flag = 1;
+                    }
+                }
+                if (*(volatile int *)&abort_flag) {
+                    ok = false;
+                    break;
+                }
+                const real *sc = sm + (P % NSTAGE) * SLOT;
+                if (active) {
+                    real cs[8], sn8[8];
+                    const real *rt = sc + NARR * WP;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        cs[i] = rt[i];
+                        sn8[i] = rt[8 + i];
+                    }
+                    site_update<real, WP, REREAD>(A, sm + ((P - 1) % NSTAGE) * SLOT, sc,
+                                                  sm + ((P + 1) % NSTAGE) * SLOT, HALO + tx, j,
+                                                  mb + c - 1, inv_r, cs, sn8);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&empty[(P - 1) % NSTAGE]);
+                    if (c == L) {
+                        mbar_arrive(&empty[P % NSTAGE]);
+                        mbar_arrive(&empty[(P + 1) % NSTAGE]);
+                    }
+                }
+            }
+            base += L + 2;
+        }
+    }
+    __syncthreads();
+    if (abort_flag && tx == 0) {
+        // Drain: wait (bounded) for the copies of the last NSTAGE positions.
+        const long long n = issued_total;
+        for (long long Q = (n > NSTAGE ? n - NSTAGE : 0); Q < n; ++Q)
+            mbar_wait_bounded(&full[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1));
+    }
+}
+
+template <typename real, int W, int NSTAGE, bool REREAD, int MINB>
+__global__ void __launch_bounds__(W + 32, MINB) step_kernel_v2(const __grid_constant__ StepArgs<real> A)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    SingleWork<real, W> work{&A};
+    march2<real, W, NSTAGE, REREAD>(work, smem_raw, nullptr);
+}
+
+template <typename real, int W, int NSTAGE, bool REREAD, int MINB>
+__global__ void __launch_bounds__(W + 32, MINB) batch_step_kernel_v2(const __grid_constant__ BatchArgs<real> B)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(16) StepArgs<real> sargs2[2];
+    BatchWork<real, W> work{B.slots, B.items, *B.n_items, *B.T + B.s};
+    march2<real, W, NSTAGE, REREAD>(work, smem_raw, sargs2);
+}
+
+template <typename real, int W, int NSTAGE>
+constexpr int smem_bytes_v2()
+{
+    return (int)(sizeof(real) * NSTAGE * (NARR * (W + 2 * Halo<real>::value) + 16) + 16 * NSTAGE);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,7 +1,11 @@
-// FP32 kernels: 128 radial sites per CTA, 6-deep row ring (111 KB shared).
+// FP32 kernels.  Variants (id, pipeline, radial sites per CTA, ring depth,
+// re-read f from shared memory, min CTAs per SM):
+//   1  v1  128  6  no   2   CTA-wide barrier per row (111 KB shared)
+//   2  v2  128  6  no   2   producer warp + full/empty mbarriers (111 KB)
+//   3  v2  128  4  yes  3   as 2 with a 4-deep ring (74 KB) and <= 136 registers
 #define DBM_REAL float
-#define DBM_W 128
-#define DBM_NSTAGE 6
+#define DBM_VARIANTS(X) X(1, 1, 128, 6, false, 2) X(2, 2, 128, 6, false, 2) X(3, 2, 128, 4, true, 3)
+#define DBM_DEFAULT_VARIANT 2
 #include "dbm_launch_impl.cuh"
 
 namespace dbm {

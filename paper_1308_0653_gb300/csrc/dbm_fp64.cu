@@ -1,5 +1,8 @@
-// FP64 kernels: 64 radial sites per CTA, 5-deep row ring (92 KB shared).
+// FP64 kernels (ALU-bound on GB300).  Variants as in the FP32 unit:
+//   1  v1  64  5  no   2
+//   2  v2  64  5  no   2
+//   3  v2  64  4  yes  3
 #define DBM_REAL double
-#define DBM_W 64
-#define DBM_NSTAGE 5
+#define DBM_VARIANTS(X) X(1, 1, 64, 5, false, 2) X(2, 2, 64, 5, false, 2) X(3, 2, 64, 4, true, 3)
+#define DBM_DEFAULT_VARIANT 2
 #include "dbm_launch_impl.cuh"

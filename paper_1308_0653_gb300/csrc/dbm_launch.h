@@ -9,17 +9,25 @@
 namespace dbm {
 
 struct KernelInfo {
-    int W;             // radial sites per CTA (= threads)
+    int W;             // radial sites per CTA
+    int threads;       // threads per CTA (W, plus a producer warp in v2)
     int nstage;        // row buffers in the shared-memory ring
     int halo;          // halo columns per side (16 bytes)
     int smem;          // dynamic shared memory per CTA (bytes)
-    int blocks_per_sm; // resident CTAs per SM at that shared-memory size
+    int blocks_per_sm; // resident CTAs per SM
+    int version;       // 1: CTA-wide row barrier, 2: producer warp + full/empty barriers
 };
 
-template <typename real> cudaError_t kernel_info(KernelInfo *out);
-template <typename real> cudaError_t launch_step(const StepArgs<real> &A, int grid, cudaStream_t s);
-template <typename real> cudaError_t batch_kernel_info(KernelInfo *out);
-template <typename real> cudaError_t launch_batch_step(const BatchArgs<real> &B, int grid, cudaStream_t s);
+constexpr int MAX_VARIANTS = 8;
+
+// Kernel variants of one precision are numbered 1..num_variants<real>().
+template <typename real> int num_variants();
+template <typename real> int default_variant();
+template <typename real> cudaError_t kernel_info(int variant, KernelInfo *out);
+template <typename real> cudaError_t launch_step(int variant, const StepArgs<real> &A, int grid, cudaStream_t s);
+template <typename real> cudaError_t batch_kernel_info(int variant, KernelInfo *out);
+template <typename real>
+cudaError_t launch_batch_step(int variant, const BatchArgs<real> &B, int grid, cudaStream_t s);
 cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const InitArgs<real> &A, cudaStream_t s);
 template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int grid, cudaStream_t s);

@@ -1,61 +1,125 @@
 // Instantiates the kernels of one precision; included once per precision
-// translation unit with DBM_REAL, DBM_W and DBM_NSTAGE defined.
+// translation unit with DBM_REAL and the variant list DBM_VARIANTS(X) defined,
+// X(id, version, W, NSTAGE, REREAD, MIN_BLOCKS_PER_SM), and DBM_DEFAULT_VARIANT.
 #include "dbm_launch.h"
 
 namespace dbm {
 
 namespace {
-constexpr int kW = DBM_W;
-constexpr int kNS = DBM_NSTAGE;
-constexpr int kHalo = Halo<DBM_REAL>::value;
-constexpr int kSmem = (int)(sizeof(DBM_REAL) * kNS * NARR * (kW + 2 * kHalo) + 8 * kNS);
-}  // namespace
 
-template <>
-cudaError_t kernel_info<DBM_REAL>(KernelInfo *out)
+template <int VER, int W, int NS, bool RR, int MB> struct Variant;
+
+template <int W, int NS, bool RR, int MB>
+struct Variant<1, W, NS, RR, MB> {
+    static constexpr int kThreads = W;
+    static constexpr int kSmem =
+        (int)(sizeof(DBM_REAL) * NS * NARR * (W + 2 * Halo<DBM_REAL>::value) + 8 * NS);
+    static void *single() { return (void *)step_kernel<DBM_REAL, W, NS>; }
+    static void *batch() { return (void *)batch_step_kernel<DBM_REAL, W, NS>; }
+    static void run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
+    {
+        step_kernel<DBM_REAL, W, NS><<<g, kThreads, kSmem, s>>>(A);
+    }
+    static void run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
+    {
+        batch_step_kernel<DBM_REAL, W, NS><<<g, kThreads, kSmem, s>>>(B);
+    }
+};
+
+template <int W, int NS, bool RR, int MB>
+struct Variant<2, W, NS, RR, MB> {
+    static constexpr int kThreads = W + 32;
+    static constexpr int kSmem = smem_bytes_v2<DBM_REAL, W, NS>();
+    static void *single() { return (void *)step_kernel_v2<DBM_REAL, W, NS, RR, MB>; }
+    static void *batch() { return (void *)batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB>; }
+    static void run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
+    {
+        step_kernel_v2<DBM_REAL, W, NS, RR, MB><<<g, kThreads, kSmem, s>>>(A);
+    }
+    static void run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
+    {
+        batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB><<<g, kThreads, kSmem, s>>>(B);
+    }
+};
+
+template <typename V>
+cudaError_t info_of(void *fn, int ver, int W, int NS, KernelInfo *out)
 {
-    auto kern = step_kernel<DBM_REAL, kW, kNS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, V::kSmem);
     if (e != cudaSuccess) return e;
     int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW, kSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, V::kThreads, V::kSmem);
     if (e != cudaSuccess) return e;
-    out->W = kW;
-    out->nstage = kNS;
-    out->halo = kHalo;
-    out->smem = kSmem;
+    out->W = W;
+    out->threads = V::kThreads;
+    out->nstage = NS;
+    out->halo = Halo<DBM_REAL>::value;
+    out->smem = V::kSmem;
     out->blocks_per_sm = nb;
+    out->version = ver;
     return cudaSuccess;
 }
 
-template <>
-cudaError_t launch_step<DBM_REAL>(const StepArgs<DBM_REAL> &A, int grid, cudaStream_t s)
+}  // namespace
+
+template <> int num_variants<DBM_REAL>()
 {
-    step_kernel<DBM_REAL, kW, kNS><<<grid, kW, kSmem, s>>>(A);
+    int n = 0;
+#define X(id, ver, W, NS, RR, MB) n = n > id ? n : id;
+    DBM_VARIANTS(X)
+#undef X
+    return n;
+}
+
+template <> int default_variant<DBM_REAL>() { return DBM_DEFAULT_VARIANT; }
+
+template <>
+cudaError_t kernel_info<DBM_REAL>(int variant, KernelInfo *out)
+{
+    switch (variant) {
+#define X(id, ver, W, NS, RR, MB) \
+    case id: return info_of<Variant<ver, W, NS, RR, MB>>(Variant<ver, W, NS, RR, MB>::single(), ver, W, NS, out);
+        DBM_VARIANTS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t batch_kernel_info<DBM_REAL>(int variant, KernelInfo *out)
+{
+    switch (variant) {
+#define X(id, ver, W, NS, RR, MB) \
+    case id: return info_of<Variant<ver, W, NS, RR, MB>>(Variant<ver, W, NS, RR, MB>::batch(), ver, W, NS, out);
+        DBM_VARIANTS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_step<DBM_REAL>(int variant, const StepArgs<DBM_REAL> &A, int grid, cudaStream_t s)
+{
+    switch (variant) {
+#define X(id, ver, W, NS, RR, MB) \
+    case id: Variant<ver, W, NS, RR, MB>::run(A, grid, s); break;
+        DBM_VARIANTS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
 template <>
-cudaError_t batch_kernel_info<DBM_REAL>(KernelInfo *out)
+cudaError_t launch_batch_step<DBM_REAL>(int variant, const BatchArgs<DBM_REAL> &B, int grid, cudaStream_t s)
 {
-    auto kern = batch_step_kernel<DBM_REAL, kW, kNS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    int nb = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kW, kSmem);
-    if (e != cudaSuccess) return e;
-    out->W = kW;
-    out->nstage = kNS;
-    out->halo = kHalo;
-    out->smem = kSmem;
-    out->blocks_per_sm = nb;
-    return cudaSuccess;
-}
-
-template <>
-cudaError_t launch_batch_step<DBM_REAL>(const BatchArgs<DBM_REAL> &B, int grid, cudaStream_t s)
-{
-    batch_step_kernel<DBM_REAL, kW, kNS><<<grid, kW, kSmem, s>>>(B);
+    switch (variant) {
+#define X(id, ver, W, NS, RR, MB) \
+    case id: Variant<ver, W, NS, RR, MB>::run_batch(B, grid, s); break;
+        DBM_VARIANTS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ class DbmParams(ctypes.Structure):
         ("nr", ctypes.c_int32), ("ntheta", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("reaction_energy", ctypes.c_int32),
         ("r_bc_inner", ctypes.c_int32), ("r_bc_outer", ctypes.c_int32),
-        ("rows_per_item", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("rows_per_item", ctypes.c_int32), ("variant", ctypes.c_int32),
         ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
         ("dt", ctypes.c_double), ("tau", ctypes.c_double),
         ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
@@ -81,7 +81,11 @@ def lib():
         L.dbm_status.argtypes = [H, vp]
         L.dbm_export_state.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.dbm_import_state.argtypes = [H, vp, vp, ctypes.c_int64, vp]
-        L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 5
+        L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 6
+        L.dbm_num_variants.argtypes = [ctypes.c_int]
+        L.dbm_set_variant.argtypes = [H, ctypes.c_int]
+        L.dbm_autotune.argtypes = [H, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_float)]
         B = ctypes.c_void_p
         L.dbm_batch_bytes.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int]
         L.dbm_batch_bytes.restype = ctypes.c_size_t
@@ -212,10 +216,26 @@ def dbm_import_state(h, f, lam, steps: int, stream=None):
 
 
 def dbm_launch_info(h) -> dict:
-    vals = [ctypes.c_int(0) for _ in range(5)]
+    vals = [ctypes.c_int(0) for _ in range(6)]
     _check(lib().dbm_launch_info(h, *[ctypes.byref(v) for v in vals]), "dbm_launch_info")
-    return dict(zip(("grid", "threads", "smem_bytes", "rows_per_item", "items"),
+    return dict(zip(("grid", "threads", "smem_bytes", "rows_per_item", "items", "variant"),
                     [v.value for v in vals]))
+
+
+def dbm_num_variants(precision: int) -> int:
+    return int(lib().dbm_num_variants(int(precision)))
+
+
+def dbm_set_variant(h, variant: int):
+    _check(lib().dbm_set_variant(h, int(variant)), "dbm_set_variant")
+
+
+def dbm_autotune(h, steps: int, stream=None):
+    """Returns (best variant, [ms per step of variants 1..8; unused entries 0])."""
+    best = ctypes.c_int(0)
+    ms = (ctypes.c_float * 8)()
+    _check(lib().dbm_autotune(h, int(steps), _stream(stream), ctypes.byref(best), ms), "dbm_autotune")
+    return best.value, [ms[i] for i in range(8)]
 
 
 def dbm_batch_bytes(max_slots: int, max_items: int, precision: int) -> int:
@@ -283,6 +303,7 @@ def params_from(d: dict) -> DbmParams:
     p.precision = _PREC[d.get("precision", "fp32")]
     p.reaction_energy = _RE[d.get("reaction_energy", 0)]
     p.rows_per_item = int(d.get("rows_per_item", 0))
+    p.variant = int(d.get("variant", 0))
     return p
 
 
@@ -327,6 +348,13 @@ class Simulation:
 
     def launch_info(self) -> dict:
         return dbm_launch_info(self.h)
+
+    def set_variant(self, variant: int):
+        dbm_set_variant(self.h, variant)
+
+    def autotune(self, steps: int = 20, stream=None):
+        best, ms = dbm_autotune(self.h, steps, stream)
+        return best, ms[:dbm_num_variants(self.p.precision)]
 
     def export_state(self, stream=None):
         dt = np.float64 if self.p.precision == DBM_FP64 else np.float32
@@ -396,6 +424,144 @@ class Batch:
         if self.b is not None:
             dbm_batch_destroy(self.b)
             self.b = None
+            self.buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- serving -------------------------------------------------------------
+
+class DbmServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("quantum", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_items", ctypes.c_int64), ("rows_per_item", ctypes.c_int32),
+                ("max_bypass", ctypes.c_int32)]
+
+
+class DbmFields(ctypes.Structure):
+    _fields_ = [(k, _dp) for k in FIELDS]
+
+
+class DbmResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("nr", ctypes.c_int32), ("ntheta", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("steps", ctypes.c_int64)] + \
+               [(k, _dp) for k in FIELDS] + \
+               [("totals", ctypes.c_double * 4), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_end", ctypes.c_double)]
+
+
+class DbmServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("submitted", "completed", "failed", "cancelled",
+                                                "queued", "running", "updates",
+                                                "pool_free_largest", "batch_time")] + \
+               [("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        vp = ctypes.c_void_p
+        L.dbm_server_min_bytes.argtypes = [ctypes.POINTER(DbmServerConfig)]
+        L.dbm_server_min_bytes.restype = ctypes.c_size_t
+        L.dbm_server_create.argtypes = [ctypes.POINTER(DbmServerConfig), vp, ctypes.c_size_t,
+                                        ctypes.POINTER(vp)]
+        L.dbm_submit.argtypes = [vp, ctypes.POINTER(DbmParams), ctypes.POINTER(DbmFields),
+                                 ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+        L.dbm_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(DbmResult), ctypes.c_int64]
+        L.dbm_result_free.argtypes = [ctypes.POINTER(DbmResult)]
+        L.dbm_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.dbm_server_stats_get.argtypes = [vp, ctypes.POINTER(DbmServerStats)]
+        L.dbm_server_destroy.argtypes = [vp]
+        L._server_ready = True
+    return L
+
+
+def dbm_server_min_bytes(cfg: DbmServerConfig) -> int:
+    return int(_server_lib().dbm_server_min_bytes(ctypes.byref(cfg)))
+
+
+def dbm_server_create(cfg: DbmServerConfig, dev_ptr: int, nbytes: int):
+    s = ctypes.c_void_p()
+    _check(_server_lib().dbm_server_create(ctypes.byref(cfg), ctypes.c_void_p(dev_ptr),
+                                           ctypes.c_size_t(nbytes), ctypes.byref(s)),
+           "dbm_server_create")
+    return s
+
+
+def dbm_submit(s, params: DbmParams, fields: dict, nsteps: int) -> int:
+    arrs = {k: np.ascontiguousarray(fields[k], dtype=np.float64) for k in FIELDS}
+    f = DbmFields(*[_ptr(arrs[k]) for k in FIELDS])
+    t = ctypes.c_uint64(0)
+    _check(_server_lib().dbm_submit(s, ctypes.byref(params), ctypes.byref(f), int(nsteps),
+                                    ctypes.byref(t)), "dbm_submit")
+    return t.value
+
+
+def dbm_poll(s, ticket: int, timeout_us: int = -1):
+    """(status, result dict or None); the result's arrays are copied and freed."""
+    r = DbmResult()
+    st = _server_lib().dbm_poll(s, ctypes.c_uint64(ticket), ctypes.byref(r), int(timeout_us))
+    if st != DBM_OK:
+        return st, None
+    out = {"status": r.status, "steps": r.steps, "totals": np.array(r.totals[:]),
+           "t_submit": r.t_submit, "t_start": r.t_start, "t_end": r.t_end}
+    n = r.nr * r.ntheta
+    for k in FIELDS:
+        ptr = getattr(r, k)
+        out[k] = (np.ctypeslib.as_array(ptr, shape=(n,)).reshape(r.ntheta, r.nr).copy()
+                  if ptr else None)
+    _server_lib().dbm_result_free(ctypes.byref(r))
+    return st, out
+
+
+def dbm_cancel(s, ticket: int):
+    _check(_server_lib().dbm_cancel(s, ctypes.c_uint64(ticket)), "dbm_cancel")
+
+
+def dbm_server_stats_get(s) -> dict:
+    st = DbmServerStats()
+    _check(_server_lib().dbm_server_stats_get(s, ctypes.byref(st)), "dbm_server_stats_get")
+    return {k: getattr(st, k) for k, _ in DbmServerStats._fields_ if k != "pad"}
+
+
+def dbm_server_destroy(s):
+    _check(_server_lib().dbm_server_destroy(s), "dbm_server_destroy")
+
+
+class Server:
+    """A serving loop on a torch device pool borrowed by the library."""
+
+    def __init__(self, pool_bytes: int, max_slots=16, max_queue=1024, quantum=64,
+                 precision="fp32", max_items=1 << 16, rows_per_item=16, max_bypass=8, device=None):
+        import torch
+        self.cfg = DbmServerConfig(max_slots, max_queue, quantum, _PREC[precision], max_items,
+                                   rows_per_item, max_bypass)
+        dev = torch.device("cuda" if device is None else device)
+        self.buf = torch.empty(int(pool_bytes) + 256, dtype=torch.uint8, device=dev)
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+        self.s = dbm_server_create(self.cfg, self.ptr, int(pool_bytes))
+
+    def submit(self, params, fields, nsteps) -> int:
+        p = params if isinstance(params, DbmParams) else params_from(params)
+        return dbm_submit(self.s, p, fields, nsteps)
+
+    def poll(self, ticket, timeout_us=-1):
+        return dbm_poll(self.s, ticket, timeout_us)
+
+    def cancel(self, ticket):
+        dbm_cancel(self.s, ticket)
+
+    def stats(self) -> dict:
+        return dbm_server_stats_get(self.s)
+
+    def close(self):
+        if self.s is not None:
+            dbm_server_destroy(self.s)
+            self.s = None
             self.buf = None
 
     def __del__(self):

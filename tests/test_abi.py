@@ -70,7 +70,8 @@ def test_check_reports_the_courant_number():
 @pytest.mark.parametrize("field,value", [("nr", 0), ("ntheta", -1), ("r_in", 0.0), ("r_out", 0.01),
                                          ("dt", 0.0), ("tau", 0.0), ("omega1", -1.0),
                                          ("precision", 7), ("reaction_energy", 3),
-                                         ("rows_per_item", -2), ("reserved", 1)])
+                                         ("rows_per_item", -2), ("variant", 99),
+                                         ("variant", -1)])
 def test_check_rejects_invalid_parameters(field, value):
     p = dbm.dbm_params_default()
     setattr(p, field, value)
@@ -114,3 +115,17 @@ def test_null_handles_are_rejected():
     assert L.dbm_destroy(None) == dbm.DBM_EINVAL
     assert L.dbm_moments(None, None, None, None, None, None, None, None) == dbm.DBM_EINVAL
     assert L.dbm_steps_done(None) == -1
+
+
+def test_variants_are_numbered_per_precision():
+    for prec in (dbm.DBM_FP32, dbm.DBM_FP64):
+        n = dbm.dbm_num_variants(prec)
+        assert n >= 2
+        p = dbm.dbm_params_default()
+        p.precision = prec
+        for v in range(0, n + 1):
+            p.variant = v
+            assert dbm.dbm_check(p)[0] == dbm.DBM_OK
+        p.variant = n + 1
+        assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL
+    assert dbm.dbm_num_variants(7) == 0
