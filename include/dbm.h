@@ -206,6 +206,36 @@ int dbm_set_variant(dbm_t *h, int variant);
  * the chosen variant, ms_per_step[v-1] (may be NULL) each variant's time. */
 int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_step);
 
+/* ---- allocation-free conservation totals -------------------------------- */
+/*
+ * The paper has no counterpart to this entry point.  It computes the same FP64
+ * totals as dbm_moments for callers that cannot hand the library any device
+ * scratch memory: a component holding only raw device pointers to a state that
+ * another component owns (a checkpoint writer or a monitoring thread), or code
+ * under a fixed device-memory budget whose allocator refuses new allocations
+ * once a run has started.  It allocates nothing and calls no cudaMalloc,
+ * cudaFree or allocating library routine: its reduction scratch (4 FP64 sums
+ * per theta row) is a static device array of DBM_NOALLOC_MAX_ROWS rows
+ * (512 KB) that every GPU loading the library holds until the process exits.
+ *
+ *   d_f       device array f[33][ntheta][nr] in p->precision (float or double),
+ *             the layout dbm_export_state writes; read in stream order.
+ *   d_totals  device array of 4 doubles receiving {mass, momentum_x,
+ *             momentum_y, energy}, area-weighted as in dbm_moments.
+ *   stream    cudaStream_t as void* (NULL: legacy default stream); the call
+ *             only enqueues two kernels and returns.
+ *
+ * The first call on a device looks up the device address of the static array
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; each
+ * call rewrites every row it reads, so nothing needs clearing, but calls whose
+ * work overlaps on the GPU (for example on two concurrent streams) race on it.
+ * Errors: DBM_EINVAL (NULL pointer or invalid grid/precision), DBM_ENOMEM
+ * (ntheta > DBM_NOALLOC_MAX_ROWS: the state does not fit the static scratch),
+ * DBM_ECUDA (symbol lookup or launch failed). */
+#define DBM_NOALLOC_MAX_ROWS 16384
+int dbm_totals_noalloc(const dbm_params *p, const void *d_f, double *d_totals, void *stream);
+
 /* ---- batches: many uneven simulations, one persistent launch per step ---- */
 /*
  * A batch advances the simulations attached to its slots together: each time

@@ -17,7 +17,7 @@ LIB = os.path.join(OUT, "libdbm.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]
-UNITS = ["dbm_fp32.cu", "dbm_fp64.cu", "dbm_api.cu", "dbm_server.cu"]
+UNITS = ["dbm_fp32.cu", "dbm_fp64.cu", "dbm_api.cu", "dbm_server.cu", "dbm_noalloc.cu"]
 
 
 def _sources():
