@@ -189,6 +189,11 @@ int dbm_import_state(dbm_t *h, const void *f, const void *lam, int64_t steps, vo
 int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes,
                     int *rows_per_item, int *items, int *variant);
 
+/* Self-test of the FP32 step's reciprocal (hardware approximation refined by
+ * one Newton-Raphson step): writes it and the correctly rounded 1/x for n
+ * device floats d_x into d_approx and d_ieee (device arrays); asynchronous. */
+int dbm_selftest_rcp(const float *d_x, float *d_approx, float *d_ieee, int n, void *stream);
+
 /* Number of step-kernel variants for a precision (0 if invalid).  Variants
  * differ only in how the work is staged (pipeline, ring depth, registers);
  * every variant computes the same update bit for bit. */

@@ -171,6 +171,7 @@ void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
         A.decay = (real)std::exp(-p.dt / p.tau);
         A.one_m_decay = (real)(-std::expm1(-p.dt / p.tau));
         A.dt = (real)p.dt;
+        A.inv_dt = (real)(1.0 / p.dt);
         A.Q = (real)p.Q;
         A.omega1 = (real)p.omega1;
         A.omega2 = (real)p.omega2;
@@ -681,6 +682,14 @@ int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes, in
     if (smem_bytes) *smem_bytes = h->ki.smem;
     if (rows_per_item) *rows_per_item = h->rows_per_item;
     if (items) *items = h->items;
+    return DBM_OK;
+}
+
+int dbm_selftest_rcp(const float *d_x, float *d_approx, float *d_ieee, int n, void *stream)
+{
+    if (!d_x || !d_approx || !d_ieee || n < 0) return DBM_EINVAL;
+    cudaError_t e = launch_rcp_selftest(d_x, d_approx, d_ieee, n, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "rcp self-test launch");
     return DBM_OK;
 }
 

@@ -57,6 +57,7 @@ struct StepArgs {
     real decay;           // exp(-dt / tau)
     real one_m_decay;     // 1 - exp(-dt / tau)
     real dt, Q, omega1, omega2, m_exp, n_exp, T_th;
+    real inv_dt;          // 1 / dt
     real v[4], v2[4];     // ring speeds and their squares
     real Fc[4][4];        // F_k(T) = T (Fc[k][0] + T (Fc[k][1] + T (Fc[k][2] + T Fc[k][3])))
 };
@@ -159,6 +160,17 @@ template <> struct Op<float> {
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    // 1/x for normal, finite x of moderate size (densities, temperatures):
+    // the hardware's approximate reciprocal refined by one Newton-Raphson
+    // step for f(r) = 1/r - x, r1 = r0 + r0 (1 - x r0).  Branch-free; its
+    // error against the correctly rounded reciprocal is checked on the GPU.
+    static __device__ __forceinline__ float rcp(float x)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        const float e = __fmaf_rn(-x, r, 1.0f);
+        return __fmaf_rn(r, e, r);
+    }
 };
 template <> struct Op<double> {
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -166,6 +178,7 @@ template <> struct Op<double> {
     static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
     static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double x) { return __ddiv_rn(1.0, x); }
 };
 
 // ---------------------------------------------------------------------------
@@ -207,11 +220,11 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
         jy = O::fma(A.v[k], sy, jy);
         e2 = O::fma(A.v2[k], s0, e2);
     }
-    const real inv_rho = O::div(one, rho);
+    const real inv_rho = O::rcp(rho);
     const real ux = O::mul(jx, inv_rho), uy = O::mul(jy, inv_rho);
     const real u2 = O::fma(ux, ux, O::mul(uy, uy));
     const real T = O::mul(half, O::sub(O::mul(e2, inv_rho), u2));
-    const real inv_T = O::div(one, T);
+    const real inv_T = O::rcp(T);
 
     // --- a3: weights F_k(T), F_0 = 1 - 8 sum F_k ---------------------------
     real F[4];
@@ -260,9 +273,9 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     if (sab > real(0)) {
         // lam+ - lam = (1-lam)(a+b lam)(E-1) / [(a+b) + (a+b lam)(E-1)], E = e^{(a+b)dt}
         const real em1 = expm1_(O::mul(sab, A.dt));
-        dlam = O::div(O::mul(O::mul(om, g), em1), O::fma(g, em1, sab));
+        dlam = O::mul(O::mul(O::mul(om, g), em1), O::rcp(O::fma(g, em1, sab)));
     }
-    if (A.reaction_energy) R = O::div(dlam, A.dt);
+    if (A.reaction_energy) R = O::mul(dlam, A.inv_dt);
 
     // --- a6+a7 coefficients: f_new = poly(xi) (beta_k - gamma_k xi) + ... ---
     //     M = f^eq ((v-u)^2 - 2T) / (2T^2) Q R with (v-u)^2 = v_k^2 + u^2 - 2 T xi
@@ -588,7 +601,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + sizeof(real) * NSTAGE * SLOT);
     uint64_t *empty = full + NSTAGE;
     __shared__ int abort_flag;
-    __shared__ long long issued_total;
+    __shared__ int issued_total;
 
     const int tx = threadIdx.x;
     const int warp = tx >> 5, lane = tx & 31;
@@ -607,25 +620,25 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
 
     if (warp == NCW) {
         // ------------------------------ producer ------------------------------
-        long long total_loads = 0;
+        int total_loads = 0;  // ring positions of this CTA (32-bit: cheap slot arithmetic)
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             const StepArgs<real> *a;
             int j0, mb, me;
             if (work.item(it, a, j0, mb, me)) total_loads += (me - mb) + 2;
         }
-        long long issued = 0;
+        int issued = 0;
         int p_item = blockIdx.x, p_row = 0;
         const StepArgs<real> *pa = nullptr;
         int pj0 = 0, pmb = 0, pme = 0;
         bool p_ok = false;
         while (issued < total_loads) {
-            const int slot = (int)(issued % NSTAGE);
+            const int slot = issued % NSTAGE;
             while (!p_ok) {
                 p_ok = work.item(p_item, pa, pj0, pmb, pme);
                 if (!p_ok) p_item += gridDim.x;
             }
             if (issued >= NSTAGE) {
-                const uint32_t par = (uint32_t)(((issued / NSTAGE) - 1) & 1);
+                const uint32_t par = (uint32_t)((issued / NSTAGE - 1) & 1);
                 if (!mbar_wait_bounded(&empty[slot], par)) {
                     if (lane == 0) atomicOr(pa->status, ST_WAIT_TIMEOUT);
                     abort_flag = 1;
@@ -660,7 +673,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         if (lane == 0) issued_total = issued;
     } else {
         // ------------------------------ consumers -----------------------------
-        long long base = 0;
+        int base = 0;
         int parity = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
@@ -686,8 +699,8 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
             const bool active = j < A.nr;
             const real inv_r = A.inv_r[active ? j : 0];
             for (int c = 1; c <= L; ++c) {
-                const long long P = base + c;
-                for (long long Q = (c == 1 ? P - 1 : P + 1); Q <= P + 1; ++Q) {
+                const int P = base + c;
+                for (int Q = (c == 1 ? P - 1 : P + 1); Q <= P + 1; ++Q) {
                     if (!mbar_wait_bounded(&full[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1))) {
                         if (lane == 0) atomicOr(A.status, ST_WAIT_TIMEOUT);
                         abort_flag = 1;
@@ -725,8 +738,8 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
     __syncthreads();
     if (abort_flag && tx == 0) {
         // Drain: wait (bounded) for the copies of the last NSTAGE positions.
-        const long long n = issued_total;
-        for (long long Q = (n > NSTAGE ? n - NSTAGE : 0); Q < n; ++Q)
+        const int n = issued_total;
+        for (int Q = (n > NSTAGE ? n - NSTAGE : 0); Q < n; ++Q)
             mbar_wait_bounded(&full[Q % NSTAGE], (uint32_t)((Q / NSTAGE) & 1));
     }
 }
@@ -752,6 +765,15 @@ template <typename real, int W, int NSTAGE>
 constexpr int smem_bytes_v2()
 {
     return (int)(sizeof(real) * NSTAGE * (NARR * (W + 2 * Halo<real>::value) + 16) + 16 * NSTAGE);
+}
+
+// Self-test of Op<float>::rcp against the correctly rounded division.
+static __global__ void rcp_selftest_kernel(const float *x, float *approx, float *ieee, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        approx[i] = Op<float>::rcp(x[i]);
+        ieee[i] = __fdiv_rn(1.0f, x[i]);
+    }
 }
 
 // ---------------------------------------------------------------------------

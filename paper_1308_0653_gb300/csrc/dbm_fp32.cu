@@ -15,6 +15,12 @@ cudaError_t launch_totals(const double *partials, int nblocks, double *totals, c
     return cudaGetLastError();
 }
 
+cudaError_t launch_rcp_selftest(const float *x, float *approx, float *ieee, int n, cudaStream_t s)
+{
+    rcp_selftest_kernel<<<256, 256, 0, s>>>(x, approx, ieee, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s)
 {
     batch_advance_kernel<<<1, 32, 0, s>>>(T, k);
