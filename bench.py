@@ -458,6 +458,7 @@ def run_serve(args):
     wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
+    executed_glups = stats["executed"] / wall / 1e9
     lat = np.array(lat) if lat else np.array([np.nan])
     line = {"metric": METRIC + ", served", "value": upd / wall / 1e9, "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -467,6 +468,8 @@ def run_serve(args):
                        "requests": len(tickets), "pool_bytes": pool, "max_slots": 64, "quantum": 64},
             "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.nanpercentile(lat, 50)),
             "p99_s": float(np.nanpercentile(lat, 99)), "backlog": len(tickets) - int(np.isfinite(lat).sum()),
+            "executed_glups": executed_glups,
+            "offered_glups": sum(w.sites * NV * w.nsteps for _, w in tickets) / args.duration / 1e9,
             "server": stats}
     print(json.dumps(line), flush=True)
     return 0

@@ -166,6 +166,21 @@ int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, doubl
  * totals, no status check. */
 int dbm_moments_device(dbm_t *h, double *d_out, void *stream);
 
+/* Non-equilibrium manifestations of Sec. II.E (Eqs. M_absolute,
+ * D_absolute): Delta*_m = M*_m(f) - M*_m(f^eq) with the central moments
+ * M*_2 = sum f v* v*, M*_3 = sum f v* v* v*, M*_{3,1} = sum (1/2) f |v*|^2 v*,
+ * M*_{4,2} = sum (1/2) f |v*|^2 v* v*, v* = v - u, polar components,
+ * evaluated in FP64 from f.  out: host array of DBM_NONEQ * ntheta * nr
+ * doubles, [component][ntheta][nr], components rr, r-theta, theta-theta of
+ * Delta*_2; rrr, rr-theta, r-theta-theta, theta-theta-theta of Delta*_3;
+ * r, theta of Delta*_{3,1}; rr, r-theta, theta-theta of Delta*_{4,2}.
+ * Synchronises `stream`. */
+#define DBM_NONEQ 12
+int dbm_noneq(dbm_t *h, double *out, void *stream);
+
+/* As dbm_noneq into device memory d_out (same layout); asynchronous. */
+int dbm_noneq_device(dbm_t *h, double *d_out, void *stream);
+
 /* Steps taken since the last init or import. */
 int64_t dbm_steps_done(const dbm_t *h);
 
@@ -342,6 +357,7 @@ typedef struct dbm_server_stats {
     double submitted, completed, failed, cancelled;
     double queued, running;
     double updates;            /* site x velocity updates of completed requests  */
+    double executed;           /* site x velocity updates enqueued in all quanta  */
     double pool_free_largest;  /* bytes                                           */
     double batch_time;         /* steps of the batch clock                        */
     int32_t status;            /* first error of the batched steps, or DBM_OK     */

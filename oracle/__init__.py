@@ -86,6 +86,9 @@ def lib():
         L.oracle_totals.argtypes = [P, dp, dp]
         L.oracle_run.argtypes = [P] + [dp] * 5 + [ctypes.c_long] + [dp] * 5
         L.oracle_run.restype = ctypes.c_int
+        L.oracle_central_moments.argtypes = [dp, ctypes.c_double, dp, ctypes.c_double,
+                                             ctypes.c_double, dp]
+        L.oracle_noneq.argtypes = [P, dp, dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_set_threads.restype = ctypes.c_int
         _lib = L
@@ -211,4 +214,23 @@ def run(p, fields, nsteps):
                           _ptr(out["T"]), _ptr(out["lam"]))
     if rc != 0:
         raise MemoryError("oracle_run: allocation failed")
+    return out
+
+
+NONEQ = ("d2_rr", "d2_rth", "d2_thth", "d3_rrr", "d3_rrth", "d3_rthth", "d3_ththth",
+         "d31_r", "d31_th", "d42_rr", "d42_rth", "d42_thth")
+
+
+def central_moments(theta, g, ur, uth, v=DEFAULTS["v"]):
+    out = np.zeros(12)
+    lib().oracle_central_moments(_ptr(_vec(v)), float(theta), _ptr(_vec(g)), float(ur), float(uth),
+                                 _ptr(out))
+    return out
+
+
+def noneq(p, f):
+    """Delta*_m of Sec. II.E at every site: array (12, ntheta, nr), components in NONEQ order."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros((12, p.ntheta, p.nr))
+    lib().oracle_noneq(ctypes.byref(p), _ptr(f), _ptr(out))
     return out

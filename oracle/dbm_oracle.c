@@ -386,6 +386,58 @@ void oracle_totals(const oracle_params *p, const double *f, double totals[4])
     totals[3] = en;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Sec. II.E: non-equilibrium manifestations.                                */
+/* ------------------------------------------------------------------------- */
+static void central_with_velocities(const double *vr, const double *vth, const double *g,
+                                    long stride, double ur, double uth, double out[12])
+{
+    for (int c = 0; c < 12; ++c) out[c] = 0.0;
+    for (int q = 0; q < NV; ++q) {
+        double gq = g[q * stride];
+        double a = vr[q] - ur, b = vth[q] - uth;  /* v* in polar components */
+        double s2 = a * a + b * b;
+        out[0] += gq * a * a;
+        out[1] += gq * a * b;
+        out[2] += gq * b * b;
+        out[3] += gq * a * a * a;
+        out[4] += gq * a * a * b;
+        out[5] += gq * a * b * b;
+        out[6] += gq * b * b * b;
+        out[7] += 0.5 * gq * s2 * a;
+        out[8] += 0.5 * gq * s2 * b;
+        out[9] += 0.5 * gq * s2 * a * a;
+        out[10] += 0.5 * gq * s2 * a * b;
+        out[11] += 0.5 * gq * s2 * b * b;
+    }
+}
+
+void oracle_central_moments(const double v[4], double theta, const double g[33], double ur,
+                            double uth, double out[12])
+{
+    double vr[NV], vth[NV];
+    oracle_velocities(v, theta, vr, vth);
+    central_with_velocities(vr, vth, g, 1, ur, uth, out);
+}
+
+void oracle_noneq(const oracle_params *p, const double *f, double *out)
+{
+    long N = (long)p->nr * p->ntheta;
+    for (int m = 0; m < p->ntheta; ++m) {
+        double vr[NV], vth[NV], feq[NV];
+        oracle_velocities(p->v, theta_of(p, m), vr, vth);
+        for (int j = 0; j < p->nr; ++j) {
+            long s = (long)m * p->nr + j;
+            double rho, ur, uth, T, mf[12], me[12];
+            moments_with_velocities(vr, vth, f + s, N, &rho, &ur, &uth, &T);
+            feq_with_velocities(p->v, vr, vth, rho, ur, uth, T, feq);
+            central_with_velocities(vr, vth, f + s, N, ur, uth, mf);
+            central_with_velocities(vr, vth, feq, 1, ur, uth, me);
+            for (int c = 0; c < 12; ++c) out[c * N + s] = mf[c] - me[c];
+        }
+    }
+}
+
 int oracle_run(const oracle_params *p, const double *rho0, const double *ur0,
                const double *uth0, const double *T0, const double *lam0, long nsteps,
                double *rho, double *ur, double *uth, double *T, double *lam)

@@ -82,6 +82,21 @@ void oracle_macro(const oracle_params *p, const double *f, const double *lam,
  * energy (rho T + rho u^2 / 2 for D = 2), each summed with weight r dr dtheta. */
 void oracle_totals(const oracle_params *p, const double *f, double totals[4]);
 
+/* Sec. II.E, Eq. (M_absolute): central moments of one site's 33 values g
+ * (f or f^eq) about the velocity u = (ur, uth), polar components:
+ * out[0..2]  M*_2      rr, rth, thth      = sum g v*_a v*_b
+ * out[3..6]  M*_3      rrr, rrth, rthth, ththth = sum g v*_a v*_b v*_c
+ * out[7..8]  M*_{3,1}  r, th              = sum (1/2) g |v*|^2 v*_a
+ * out[9..11] M*_{4,2}  rr, rth, thth      = sum (1/2) g |v*|^2 v*_a v*_b
+ * with v* = v_ki - u. */
+void oracle_central_moments(const double v[4], double theta, const double g[33], double ur,
+                            double uth, double out[12]);
+
+/* Sec. II.E, Eq. (D_absolute): Delta*_m = M*_m(f) - M*_m(f^eq) at every site,
+ * written as out[c * N + s] for the 12 components c of oracle_central_moments
+ * (N = nr * ntheta, s = m * nr + j), u and f^eq taken from f's own moments. */
+void oracle_noneq(const oracle_params *p, const double *f, double *out);
+
 /* init + nsteps steps + macro.  Returns 0, or -1 on allocation failure. */
 int oracle_run(const oracle_params *p, const double *rho0, const double *ur0,
                const double *uth0, const double *T0, const double *lam0, long nsteps,

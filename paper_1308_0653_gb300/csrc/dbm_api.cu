@@ -597,6 +597,59 @@ static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
     return DBM_OK;
 }
 
+static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
+{
+    const dbm_params &p = h->p;
+    const long long N = (long long)p.nr * p.ntheta;
+    const int grid = (int)std::min<long long>((N + 255) / 256, 4096);
+    cudaError_t e;
+    if (p.precision == DBM_FP64) {
+        MomArgs<double> A;
+        std::memset(&A, 0, sizeof(A));
+        A.f = reinterpret_cast<const double *>(h->buf + h->L.f[h->cur]);
+        A.out = d_out;
+        A.plane = h->plane;
+        A.nr = p.nr;
+        A.ntheta = p.ntheta;
+        A.ld = h->ld;
+        std::memcpy(A.v, p.v, sizeof(A.v));
+        e = launch_noneq<double>(A, grid, s);
+    } else {
+        MomArgs<float> A;
+        std::memset(&A, 0, sizeof(A));
+        A.f = reinterpret_cast<const float *>(h->buf + h->L.f[h->cur]);
+        A.out = d_out;
+        A.plane = h->plane;
+        A.nr = p.nr;
+        A.ntheta = p.ntheta;
+        A.ld = h->ld;
+        std::memcpy(A.v, p.v, sizeof(A.v));
+        e = launch_noneq<float>(A, grid, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "noneq kernel launch");
+    return DBM_OK;
+}
+
+int dbm_noneq_device(dbm_t *h, double *d_out, void *stream)
+{
+    if (!h || !d_out) return DBM_EINVAL;
+    return launch_noneq_into(h, d_out, static_cast<cudaStream_t>(stream));
+}
+
+int dbm_noneq(dbm_t *h, double *out, void *stream)
+{
+    if (!h || !out) return DBM_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t N = (size_t)h->p.nr * h->p.ntheta;
+    // staging: the free f buffer holds 33 planes >= 12 doubles per site
+    double *stage = reinterpret_cast<double *>(h->buf + h->L.f[1 - h->cur]);
+    int rc = launch_noneq_into(h, stage, s);
+    if (rc != DBM_OK) return rc;
+    CK(cudaMemcpyAsync(out, stage, 12 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DBM_OK;
+}
+
 int dbm_moments_device(dbm_t *h, double *d_out, void *stream)
 {
     if (!h || !d_out) return DBM_EINVAL;

@@ -927,6 +927,62 @@ __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
     }
 }
 
+// Non-equilibrium manifestations (Sec. II.E): Delta*_m = M*_m(f) - M*_m(f^eq)
+// in FP64 from f.  The central moments of the discrete f^eq equal the
+// Maxwellian's (M*_2 = rho T I, M*_3 = M*_{3,1} = 0, M*_{4,2} = 2 rho T^2 I for
+// D = 2), so only f's moments are summed.  out: [12][ntheta][nr] doubles in the
+// order rr, rth, thth | rrr, rrth, rthth, ththth | r, th | rr, rth, thth.
+template <typename real>
+__global__ void __launch_bounds__(256) noneq_kernel(const MomArgs<real> A)
+{
+    const long long N = (long long)A.nr * A.ntheta;
+    double cx[8], cy[8];
+    cart_dirs(cx, cy);
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
+        const real *fp = A.f + (long long)m * A.ld + j;
+        double fv[NV];
+        for (int q = 0; q < NV; ++q) fv[q] = (double)fp[(long long)q * A.plane];
+        double rho = fv[0], jx = 0.0, jy = 0.0;
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < 8; ++i) {
+                rho += fv[1 + 8 * k + i];
+                jx += fv[1 + 8 * k + i] * A.v[k] * cx[i];
+                jy += fv[1 + 8 * k + i] * A.v[k] * cy[i];
+            }
+        const double ux = jx / rho, uy = jy / rho;
+        double sth, cth;
+        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        double M[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < NV; ++q) {
+            const int k = q == 0 ? -1 : (q - 1) / 8, i = q == 0 ? 0 : (q - 1) % 8;
+            const double vx = k < 0 ? 0.0 : A.v[k] * cx[i], vy = k < 0 ? 0.0 : A.v[k] * cy[i];
+            const double dx = vx - ux, dy = vy - uy;
+            const double a = dx * cth + dy * sth, b = -dx * sth + dy * cth;  // v* polar
+            const double g = fv[q], s2 = a * a + b * b;
+            M[0] += g * a * a;
+            M[1] += g * a * b;
+            M[2] += g * b * b;
+            M[3] += g * a * a * a;
+            M[4] += g * a * a * b;
+            M[5] += g * a * b * b;
+            M[6] += g * b * b * b;
+            M[7] += 0.5 * g * s2 * a;
+            M[8] += 0.5 * g * s2 * b;
+            M[9] += 0.5 * g * s2 * a * a;
+            M[10] += 0.5 * g * s2 * a * b;
+            M[11] += 0.5 * g * s2 * b * b;
+        }
+        const double T = 0.5 * (M[0] + M[2]) / rho;  // f's own temperature
+        M[0] -= rho * T;
+        M[2] -= rho * T;
+        M[9] -= 2.0 * rho * T * T;
+        M[11] -= 2.0 * rho * T * T;
+        for (int c = 0; c < 12; ++c) A.out[c * N + s] = M[c];
+    }
+}
+
 // Sum the per-block partials in a fixed order (one block): totals[4].
 static __global__ void __launch_bounds__(256) totals_kernel(const double *partials, int nblocks, double *totals)
 {

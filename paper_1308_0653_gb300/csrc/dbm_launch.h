@@ -31,6 +31,7 @@ cudaError_t launch_batch_step(int variant, const BatchArgs<real> &B, int grid, c
 cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const InitArgs<real> &A, cudaStream_t s);
 template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int grid, cudaStream_t s);
+template <typename real> cudaError_t launch_noneq(const MomArgs<real> &A, int grid, cudaStream_t s);
 cudaError_t launch_totals(const double *partials, int nblocks, double *totals, cudaStream_t s);
 cudaError_t launch_rcp_selftest(const float *x, float *approx, float *ieee, int n, cudaStream_t s);
 

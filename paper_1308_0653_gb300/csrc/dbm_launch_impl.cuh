@@ -139,4 +139,11 @@ cudaError_t launch_moments<DBM_REAL>(const MomArgs<DBM_REAL> &A, int grid, cudaS
     return cudaGetLastError();
 }
 
+template <>
+cudaError_t launch_noneq<DBM_REAL>(const MomArgs<DBM_REAL> &A, int grid, cudaStream_t s)
+{
+    noneq_kernel<DBM_REAL><<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace dbm

@@ -306,6 +306,18 @@ void scheduler(dbm_server_t *S)
 
         // ---- 3. enqueue the next quantum --------------------------------------
         if (any_active) {
+            double work = 0.0;  // site-velocity updates this quantum will execute
+            for (int k = 0; k < S->cfg.max_slots; ++k) {
+                Request *r = S->slots[k];
+                if (!r || !r->h || r->state != RUNNING) continue;
+                const int64_t left = dbm_batch_remaining(S->batch, k);
+                if (left > 0)
+                    work += (double)r->p.nr * r->p.ntheta * DBM_NV * (double)std::min<int64_t>(left, S->cfg.quantum);
+            }
+            {
+                std::lock_guard<std::mutex> lock(S->mu);
+                S->stats.executed += work;
+            }
             const int rc = dbm_batch_step(S->batch, S->cfg.quantum, S->compute);
             if (rc == DBM_OK) {
                 cudaEventRecord(quantum_done, S->compute);

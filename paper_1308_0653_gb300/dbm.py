@@ -82,6 +82,8 @@ def lib():
         L.dbm_export_state.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.dbm_import_state.argtypes = [H, vp, vp, ctypes.c_int64, vp]
         L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 6
+        L.dbm_noneq.argtypes = [H, _dp, vp]
+        L.dbm_noneq_device.argtypes = [H, vp, vp]
         L.dbm_num_variants.argtypes = [ctypes.c_int]
         L.dbm_set_variant.argtypes = [H, ctypes.c_int]
         L.dbm_autotune.argtypes = [H, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
@@ -191,6 +193,19 @@ def dbm_moments(h, rho=None, ur=None, uth=None, T=None, lam=None, totals=None, s
 def dbm_moments_device(h, dev_out_ptr: int, stream=None):
     _check(lib().dbm_moments_device(h, ctypes.c_void_p(dev_out_ptr), _stream(stream)),
            "dbm_moments_device")
+
+
+NONEQ = ("d2_rr", "d2_rth", "d2_thth", "d3_rrr", "d3_rrth", "d3_rthth", "d3_ththth",
+         "d31_r", "d31_th", "d42_rr", "d42_rth", "d42_thth")
+
+
+def dbm_noneq(h, out, stream=None):
+    _check(lib().dbm_noneq(h, _ptr(out), _stream(stream)), "dbm_noneq")
+
+
+def dbm_noneq_device(h, dev_out_ptr: int, stream=None):
+    _check(lib().dbm_noneq_device(h, ctypes.c_void_p(dev_out_ptr), _stream(stream)),
+           "dbm_noneq_device")
 
 
 def dbm_steps_done(h) -> int:
@@ -349,6 +364,12 @@ class Simulation:
     def launch_info(self) -> dict:
         return dbm_launch_info(self.h)
 
+    def noneq(self, stream=None):
+        """Delta*_m of Sec. II.E: array (12, ntheta, nr), components in NONEQ order."""
+        out = np.empty((12,) + self.shape)
+        dbm_noneq(self.h, out, stream)
+        return out
+
     def set_variant(self, variant: int):
         dbm_set_variant(self.h, variant)
 
@@ -456,7 +477,7 @@ class DbmResult(ctypes.Structure):
 
 class DbmServerStats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("submitted", "completed", "failed", "cancelled",
-                                                "queued", "running", "updates",
+                                                "queued", "running", "updates", "executed",
                                                 "pool_free_largest", "batch_time")] + \
                [("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
 

@@ -59,10 +59,13 @@ MUTANTS = [
     ("theta grid shifted", "return m * (2.0 * PI / p->ntheta);", "return (m + 0.5) * (2.0 * PI / p->ntheta);"),
     ("lambda clamp bound", "if (ln > 1.0) { ln = 1.0; ++clamped; }", "if (ln > 0.9) { ln = 0.9; ++clamped; }"),
     ("outer ghost reflects", "return j < p->nr - 1 ? j + 1 : p->nr - 1;", "return j < p->nr - 1 ? j + 1 : p->nr - 2;"),
+    ("M*_{3,1} component", "out[7] += 0.5 * gq * s2 * a;", "out[7] += 0.5 * gq * s2 * b;"),
+    ("M*_{4,2} factor", "out[9] += 0.5 * gq * s2 * a * a;", "out[9] += gq * s2 * a * a;"),
+    ("M*_3 index", "out[5] += gq * a * b * b;", "out[5] += gq * a * a * b;"),
 ]
 
 PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",
-             "tests/test_oracle_step.py", "tests/test_oracle_cj.py"]
+             "tests/test_oracle_step.py", "tests/test_oracle_noneq.py", "tests/test_oracle_cj.py"]
 
 
 def _run_pins(name, old, new):
