@@ -35,12 +35,14 @@ class OracleParams(ctypes.Structure):
         ("T_th", ctypes.c_double),
         ("v", ctypes.c_double * 4),
         ("reaction_energy", ctypes.c_int),
+        ("sector", ctypes.c_int),
+        ("r_bc_inner", ctypes.c_int),
     ]
 
 
 DEFAULTS = dict(r_in=0.05, r_out=1.05, dt=1e-5, tau=1e-3, Q=1.0, omega1=0.0,
                 omega2=0.0, m=1.0, n=1.0, T_th=1.1, v=(1.5, 3.5, 7.5, 12.5),
-                reaction_energy=0)
+                reaction_energy=0, sector=0, r_bc_inner=0)
 
 
 def make_params(**kw) -> OracleParams:
@@ -56,6 +58,9 @@ def make_params(**kw) -> OracleParams:
         p.v[i] = float(val)
     re = d["reaction_energy"]
     p.reaction_energy = {"explicit": 0, "consistent": 1}.get(re, re)
+    p.sector = int(d["sector"])
+    bc = d["r_bc_inner"]
+    p.r_bc_inner = {"outflow": 0, "centre": 1}.get(bc, bc)
     return p
 
 

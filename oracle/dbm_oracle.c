@@ -219,7 +219,10 @@ double oracle_lambda_react(double lam, double a, double b, double dt)
 /* Initial state.  READING: f starts at f^eq of the given fields (the paper  */
 /* gives macroscopic initial data only).                                     */
 /* ------------------------------------------------------------------------- */
-static double theta_of(const oracle_params *p, int m) { return m * (2.0 * PI / p->ntheta); }
+/* Sec. II.D: the domain is a full annulus/disc (theta span 2 pi) or, as in the
+ * paper's runs, a sector of 1/8 of it (span pi/4). */
+static double dtheta_of(const oracle_params *p) { return (p->sector ? PI / 4.0 : 2.0 * PI) / p->ntheta; }
+static double theta_of(const oracle_params *p, int m) { return m * dtheta_of(p); }
 static double r_of(const oracle_params *p, int j)
 {
     double dr = (p->r_out - p->r_in) / p->nr;
@@ -246,21 +249,84 @@ void oracle_init(const oracle_params *p, const double *rho, const double *ur,
 /* ------------------------------------------------------------------------- */
 /* One time step.                                                            */
 /* ------------------------------------------------------------------------- */
-/* Neighbour indices.  theta is periodic (Sec. II.D).  READING for the radial
- * boundaries (the paper defers them to its Ref. XuLin2014): zero-gradient
- * outflow, i.e. the ghost value at j = -1 (j = nr) equals the value at j = 0
- * (j = nr - 1), same theta and same velocity. */
-static int jm1(int j) { return j > 0 ? j - 1 : 0; }
-static int jp1(const oracle_params *p, int j) { return j < p->nr - 1 ? j + 1 : p->nr - 1; }
-static int mm1(const oracle_params *p, int m) { return m > 0 ? m - 1 : p->ntheta - 1; }
-static int mp1(const oracle_params *p, int m) { return m < p->ntheta - 1 ? m + 1 : 0; }
+/* Neighbour values (Sec. II.D).
+ * theta: periodic.  On a full 2 pi grid row -1 is row ntheta-1.  READING for a
+ * pi/4 sector: with the velocity set fixed in the Cartesian frame, the periodic
+ * image of the point below row 0 is the point at row ntheta-1 rotated by
+ * +pi/4, where direction i has become i+1 (Fig. 1 shows the same rotation
+ * between sectors); above the last row it is row 0 with i-1.
+ * r, outer boundary and inner boundary of an annulus: READING (the paper defers
+ * them to its Ref. XuLin2014): zero-gradient outflow, the ghost at j = -1
+ * (j = nr) equals j = 0 (j = nr - 1), same theta and velocity.
+ * r, disc centre (r_in = 0): the ghost at j = -1 (r = -dr/2) is the point at
+ * r = +dr/2 on the opposite side of the centre.  In a sector that is the
+ * paper's rule f(i_r) = f(1 - i_r) with i -> i+4 (same theta index); on a full
+ * grid it is row m + ntheta/2 with the same velocity. */
+static int vrot(int q, int s)
+{
+    if (q == 0) return 0;
+    int k = (q - 1) / 8, i = (q - 1) % 8;
+    return 1 + 8 * k + (((i + s) % 8) + 8) % 8;
+}
+
+static long at(const oracle_params *p, long N, int q, int m, int j)
+{
+    return q * N + (long)m * p->nr + j;
+}
+
+static double f_inner(const oracle_params *p, const double *f, long N, int q, int m, int j)
+{
+    if (j > 0) return f[at(p, N, q, m, j - 1)];
+    if (p->r_bc_inner == 1) {
+        if (p->sector) return f[at(p, N, vrot(q, 4), m, 0)];
+        return f[at(p, N, q, (m + p->ntheta / 2) % p->ntheta, 0)];
+    }
+    return f[at(p, N, q, m, 0)];
+}
+
+static double f_outer(const oracle_params *p, const double *f, long N, int q, int m, int j)
+{
+    return f[at(p, N, q, m, j < p->nr - 1 ? j + 1 : p->nr - 1)];
+}
+
+static double f_below(const oracle_params *p, const double *f, long N, int q, int m, int j)
+{
+    if (m > 0) return f[at(p, N, q, m - 1, j)];
+    return f[at(p, N, p->sector ? vrot(q, 1) : q, p->ntheta - 1, j)];
+}
+
+static double f_above(const oracle_params *p, const double *f, long N, int q, int m, int j)
+{
+    if (m < p->ntheta - 1) return f[at(p, N, q, m + 1, j)];
+    return f[at(p, N, p->sector ? vrot(q, -1) : q, 0, j)];
+}
+
+/* lambda is a scalar: the same neighbours without the velocity rotation. */
+static double l_inner(const oracle_params *p, const double *lam, int m, int j)
+{
+    if (j > 0) return lam[(long)m * p->nr + j - 1];
+    if (p->r_bc_inner == 1 && !p->sector) return lam[(long)((m + p->ntheta / 2) % p->ntheta) * p->nr];
+    return lam[(long)m * p->nr];
+}
+static double l_outer(const oracle_params *p, const double *lam, int m, int j)
+{
+    return lam[(long)m * p->nr + (j < p->nr - 1 ? j + 1 : p->nr - 1)];
+}
+static double l_below(const oracle_params *p, const double *lam, int m, int j)
+{
+    return lam[(long)(m > 0 ? m - 1 : p->ntheta - 1) * p->nr + j];
+}
+static double l_above(const oracle_params *p, const double *lam, int m, int j)
+{
+    return lam[(long)(m < p->ntheta - 1 ? m + 1 : 0) * p->nr + j];
+}
 
 long oracle_step(const oracle_params *p, const double *f, const double *lam,
                  double *f_new, double *lam_new)
 {
     const long N = (long)p->nr * p->ntheta;
     const double dr = (p->r_out - p->r_in) / p->nr;
-    const double dth = 2.0 * PI / p->ntheta;
+    const double dth = dtheta_of(p);
     const double dt = p->dt;
     long clamped = 0;
 
@@ -303,18 +369,17 @@ long oracle_step(const oracle_params *p, const double *f, const double *lam,
              * Eq. (Eqlambda) does with its explicit minus sign. */
             const double decay = exp(-dt / p->tau);
             for (int q = 0; q < NV; ++q) {
-                const double *fq = f + q * N;
                 double Cr = vr[q] * dt / dr;
                 double Ct = vth[q] * dt / (r * dth);
                 double fr_star, ft_star;
                 if (Cr >= 0.0)
-                    fr_star = Cr * (fq[(long)m * p->nr + j] - fq[(long)m * p->nr + jm1(j)]);
+                    fr_star = Cr * (fs[q] - f_inner(p, f, N, q, m, j));
                 else
-                    fr_star = Cr * (fq[(long)m * p->nr + jp1(p, j)] - fq[(long)m * p->nr + j]);
+                    fr_star = Cr * (f_outer(p, f, N, q, m, j) - fs[q]);
                 if (Ct >= 0.0)
-                    ft_star = Ct * (fq[(long)m * p->nr + j] - fq[(long)mm1(p, m) * p->nr + j]);
+                    ft_star = Ct * (fs[q] - f_below(p, f, N, q, m, j));
                 else
-                    ft_star = Ct * (fq[(long)mp1(p, m) * p->nr + j] - fq[(long)m * p->nr + j]);
+                    ft_star = Ct * (f_above(p, f, N, q, m, j) - fs[q]);
                 f_new[q * N + s] = feq[q] + (fs[q] - feq[q]) * decay - fr_star - ft_star
                                  + M[q] * dt;
             }
@@ -322,13 +387,13 @@ long oracle_step(const oracle_params *p, const double *f, const double *lam,
             /* Upwind lambda advection with u_r, u_theta from f (Eq. Eqlambda). */
             double lr_star, lt_star;
             if (ur >= 0.0)
-                lr_star = -ur * (lam[s] - lam[(long)m * p->nr + jm1(j)]) / dr * dt;
+                lr_star = -ur * (lam[s] - l_inner(p, lam, m, j)) / dr * dt;
             else
-                lr_star = -ur * (lam[(long)m * p->nr + jp1(p, j)] - lam[s]) / dr * dt;
+                lr_star = -ur * (l_outer(p, lam, m, j) - lam[s]) / dr * dt;
             if (uth >= 0.0)
-                lt_star = -uth * (lam[s] - lam[(long)mm1(p, m) * p->nr + j]) / (r * dth) * dt;
+                lt_star = -uth * (lam[s] - l_below(p, lam, m, j)) / (r * dth) * dt;
             else
-                lt_star = -uth * (lam[(long)mp1(p, m) * p->nr + j] - lam[s]) / (r * dth) * dt;
+                lt_star = -uth * (l_above(p, lam, m, j) - lam[s]) / (r * dth) * dt;
             double ln = lam_react + lr_star + lt_star;
             /* READING: lambda is a mass fraction (Sec. III.A), kept in [0, 1]. */
             if (ln < 0.0) { ln = 0.0; ++clamped; }
@@ -363,7 +428,7 @@ void oracle_totals(const oracle_params *p, const double *f, double totals[4])
 {
     long N = (long)p->nr * p->ntheta;
     double dr = (p->r_out - p->r_in) / p->nr;
-    double dth = 2.0 * PI / p->ntheta;
+    double dth = dtheta_of(p);
     double mass = 0.0, px = 0.0, py = 0.0, en = 0.0;
     for (int m = 0; m < p->ntheta; ++m) {
         double th = theta_of(p, m);

@@ -11,7 +11,8 @@
  * Conventions (they are the documented interface of the library as well, so
  * arrays can be compared element by element; the code is independent):
  *   - grid: cell-centred r_j = r_in + (j + 1/2) dr, dr = (r_out - r_in)/nr,
- *           theta_m = m dtheta, dtheta = 2 pi / ntheta, j in [0,nr), m in [0,ntheta)
+ *           theta_m = m dtheta, dtheta = span / ntheta (span 2 pi, or pi/4 for a
+ *           sector), j in [0,nr), m in [0,ntheta)
  *   - macroscopic fields: row-major [ntheta][nr]
  *   - distribution: f[v][ntheta][nr], v = 0 for the rest particle (k = 0),
  *           v = 1 + 8 (k - 1) + i for ring k = 1..4 and direction i = 0..7.
@@ -35,6 +36,8 @@ typedef struct oracle_params {
     double T_th;             /* ignition temperature                           */
     double v[4];             /* ring speeds v_1..v_4                           */
     int reaction_energy;     /* 0: R(lambda^t) in M (paper); 1: R = dlambda/dt */
+    int sector;              /* 0: full 2 pi grid; 1: pi/4 sector (Sec. II.D)   */
+    int r_bc_inner;          /* 0: zero-gradient outflow; 1: disc centre (r_in = 0) */
 } oracle_params;
 
 /* Sec. II.B: F_k(T), k = 0..4 (the quartic weights of the D2V33 equilibrium). */

@@ -46,26 +46,37 @@ MUTANTS = [
     ("BGK sign", "(fs[q] - feq[q]) * decay", "(feq[q] - fs[q]) * decay"),
     ("BGK rate", "const double decay = exp(-dt / p->tau);",
      "const double decay = exp(-2.0 * dt / p->tau);"),
-    ("lambda advection sign", "lr_star = -ur * (lam[s] - lam[(long)m * p->nr + jm1(j)]) / dr * dt;",
-     "lr_star = ur * (lam[s] - lam[(long)m * p->nr + jm1(j)]) / dr * dt;"),
+    ("lambda advection sign", "lr_star = -ur * (lam[s] - l_inner(p, lam, m, j)) / dr * dt;",
+     "lr_star = ur * (lam[s] - l_inner(p, lam, m, j)) / dr * dt;"),
     ("lambda theta advection without r",
-     "lt_star = -uth * (lam[s] - lam[(long)mm1(p, m) * p->nr + j]) / (r * dth) * dt;",
-     "lt_star = -uth * (lam[s] - lam[(long)mm1(p, m) * p->nr + j]) / (dth) * dt;"),
+     "lt_star = -uth * (lam[s] - l_below(p, lam, m, j)) / (r * dth) * dt;",
+     "lt_star = -uth * (lam[s] - l_below(p, lam, m, j)) / (dth) * dt;"),
     ("velocity angle sign", "double ang = i * PI / 4.0 - theta;", "double ang = theta - i * PI / 4.0;"),
     ("v_r and v_theta swapped", "vr[vindex(k, i)] = v[k - 1] * cos(ang);\n            vth[vindex(k, i)] = v[k - 1] * sin(ang);",
      "vr[vindex(k, i)] = v[k - 1] * sin(ang);\n            vth[vindex(k, i)] = v[k - 1] * cos(ang);"),
-    ("theta wrap", "return m > 0 ? m - 1 : p->ntheta - 1;", "return m > 0 ? m - 1 : 0;"),
+    ("theta wrap", "return f[at(p, N, p->sector ? vrot(q, 1) : q, p->ntheta - 1, j)];",
+     "return f[at(p, N, p->sector ? vrot(q, 1) : q, 0, j)];"),
+    ("sector wrap rotates the wrong way", "return f[at(p, N, p->sector ? vrot(q, 1) : q, p->ntheta - 1, j)];",
+     "return f[at(p, N, p->sector ? vrot(q, -1) : q, p->ntheta - 1, j)];"),
+    ("centre rule rotation", "if (p->sector) return f[at(p, N, vrot(q, 4), m, 0)];",
+     "if (p->sector) return f[at(p, N, vrot(q, 2), m, 0)];"),
+    ("full-disc centre mirror", "return f[at(p, N, q, (m + p->ntheta / 2) % p->ntheta, 0)];",
+     "return f[at(p, N, q, m, 0)];"),
     ("r not cell-centred", "return p->r_in + (j + 0.5) * dr;", "return p->r_in + (j) * dr;"),
-    ("theta grid shifted", "return m * (2.0 * PI / p->ntheta);", "return (m + 0.5) * (2.0 * PI / p->ntheta);"),
+    ("theta grid shifted", "return m * dtheta_of(p); }", "return (m + 0.5) * dtheta_of(p); }"),
+    ("sector span", "return (p->sector ? PI / 4.0 : 2.0 * PI) / p->ntheta;",
+     "return (p->sector ? PI / 2.0 : 2.0 * PI) / p->ntheta;"),
     ("lambda clamp bound", "if (ln > 1.0) { ln = 1.0; ++clamped; }", "if (ln > 0.9) { ln = 0.9; ++clamped; }"),
-    ("outer ghost reflects", "return j < p->nr - 1 ? j + 1 : p->nr - 1;", "return j < p->nr - 1 ? j + 1 : p->nr - 2;"),
+    ("outer ghost reflects", "return f[at(p, N, q, m, j < p->nr - 1 ? j + 1 : p->nr - 1)];",
+     "return f[at(p, N, q, m, j < p->nr - 1 ? j + 1 : p->nr - 2)];"),
     ("M*_{3,1} component", "out[7] += 0.5 * gq * s2 * a;", "out[7] += 0.5 * gq * s2 * b;"),
     ("M*_{4,2} factor", "out[9] += 0.5 * gq * s2 * a * a;", "out[9] += gq * s2 * a * a;"),
     ("M*_3 index", "out[5] += gq * a * b * b;", "out[5] += gq * a * a * b;"),
 ]
 
 PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",
-             "tests/test_oracle_step.py", "tests/test_oracle_noneq.py", "tests/test_oracle_cj.py"]
+             "tests/test_oracle_step.py", "tests/test_oracle_noneq.py", "tests/test_oracle_sector.py",
+             "tests/test_oracle_cj.py"]
 
 
 def _run_pins(name, old, new):
