@@ -12,7 +12,8 @@
  *
  * Conventions shared by every entry point:
  *   grid      r_j = r_in + (j + 1/2) dr, dr = (r_out - r_in) / nr, j = 0..nr-1;
- *             theta_m = m dtheta, dtheta = 2 pi / ntheta, m = 0..ntheta-1.
+ *             theta_m = m dtheta, dtheta = span / ntheta, m = 0..ntheta-1, with
+ *             span = 2 pi, or pi/4 for a sector (dbm_params.sector).
  *   fields    host or device arrays of double, row-major [ntheta][nr]
  *             (index m * nr + j); velocities in polar components u_r, u_theta.
  *   velocity  index v = 0 for the rest particle, v = 1 + 8 (k - 1) + i for
@@ -63,8 +64,11 @@ extern "C" {
 #define DBM_FP32 0
 #define DBM_FP64 1
 
-/* radial boundary rule (Sec. II.D defers it to an earlier paper; reading) */
-#define DBM_BC_OUTFLOW 0   /* zero-gradient ghost: f(-1) = f(0), f(nr) = f(nr-1) */
+/* radial boundary rules (Sec. II.D) */
+#define DBM_BC_OUTFLOW 0   /* zero-gradient ghost: f(-1) = f(0), f(nr) = f(nr-1)  */
+                           /* (the paper defers annulus boundaries; reading)      */
+#define DBM_BC_CENTRE  1   /* disc centre, inner boundary only, needs r_in = 0 and */
+                           /* a sector: f(-1, theta, k, i) = f(0, theta, k, i+4)  */
 
 /* heat put into f by M (Sec. II.B) */
 #define DBM_R_EXPLICIT   0 /* R(lambda^t, P^t) of Eq. (Cochran): the paper's form */
@@ -81,7 +85,11 @@ typedef struct dbm_params {
     int32_t variant;           /* step-kernel variant 1..dbm_num_variants();      */
                                /* 0 = autotuned choice for the size class, else   */
                                /* the library default                             */
-    double r_in, r_out;        /* annulus radii, 0 < r_in < r_out (Sec. II.D)     */
+    int32_t sector;            /* 0: full 2 pi grid; 1: pi/4 sector whose theta   */
+                               /* wrap rotates velocities (i -> i+1 below row 0,  */
+                               /* i -> i-1 above the last row), Sec. II.D, Fig. 1 */
+    int32_t reserved;          /* must be 0                                       */
+    double r_in, r_out;        /* radii, 0 < r_in < r_out (r_in = 0: disc centre) */
     double dt, tau;            /* time step and BGK relaxation time (Sec. II.C)   */
     double Q;                  /* heat release per unit mass (Sec. II.A)          */
     double omega1, omega2;     /* Cochran rate constants, >= 0 (Eq. Cochran)      */

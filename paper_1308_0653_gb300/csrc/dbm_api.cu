@@ -98,11 +98,15 @@ void weight_coeffs(const double v[4], double Fc[4][4])
 // cos and sin of (i pi/4 - theta_m); with ntheta a multiple of 8 the angle is
 // taken from the integer index (i ntheta/8 - m) mod ntheta, so the table is
 // exactly invariant under the pi/4 rotation (m -> m + ntheta/8, i -> i + 1).
+double theta_span(const dbm_params &p) { return p.sector ? PI / 4.0 : 2.0 * PI; }
+
 void row_angles(const dbm_params &p, int m, double c[8], double s[8])
 {
     for (int i = 0; i < 8; ++i) {
         double ang;
-        if (p.ntheta % 8 == 0) {
+        if (p.sector) {
+            ang = i * PI / 4.0 - m * (PI / 4.0 / p.ntheta);
+        } else if (p.ntheta % 8 == 0) {
             long long q = ((long long)i * (p.ntheta / 8) - m) % p.ntheta;
             if (q < 0) q += p.ntheta;
             ang = 2.0 * PI * (double)q / p.ntheta;
@@ -143,7 +147,7 @@ void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
 {
     const dbm_params &p = h->p;
     const double dr = (p.r_out - p.r_in) / p.nr;
-    const double dth = 2.0 * PI / p.ntheta;
+    const double dth = theta_span(p) / p.ntheta;
     double Fc[4][4];
     weight_coeffs(p.v, Fc);
     for (int b = 0; b < 2; ++b) {
@@ -166,6 +170,8 @@ void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
         A.items = A.strips * A.segs;
         A.reaction_energy = p.reaction_energy;
         A.general_pow = (p.m == 1.0 && p.n == 1.0) ? 0 : 1;
+        A.sector = p.sector;
+        A.centre = p.r_bc_inner == DBM_BC_CENTRE ? 1 : 0;
         A.cr_scale = (real)(p.dt / dr);
         A.ct_scale = (real)(p.dt / dth);
         A.decay = (real)std::exp(-p.dt / p.tau);
@@ -369,11 +375,21 @@ int dbm_check(const dbm_params *p, double *cfl)
     if ((long long)p->nr * p->ntheta > (1LL << 40)) return DBM_EINVAL;
     if (p->precision != DBM_FP32 && p->precision != DBM_FP64) return DBM_EINVAL;
     if (p->reaction_energy != DBM_R_EXPLICIT && p->reaction_energy != DBM_R_CONSISTENT) return DBM_EINVAL;
-    if (p->r_bc_inner != DBM_BC_OUTFLOW || p->r_bc_outer != DBM_BC_OUTFLOW) return DBM_EINVAL;
+    if (p->sector != 0 && p->sector != 1) return DBM_EINVAL;
+    if (p->reserved != 0) return DBM_EINVAL;
+    if (p->r_bc_outer != DBM_BC_OUTFLOW) return DBM_EINVAL;
+    if (p->r_bc_inner == DBM_BC_CENTRE) {
+        if (!p->sector || p->r_in != 0.0) return DBM_EINVAL;  // the disc centre lives in a sector
+    } else if (p->r_bc_inner != DBM_BC_OUTFLOW) {
+        return DBM_EINVAL;
+    }
     if (p->rows_per_item < 0 || p->variant < 0) return DBM_EINVAL;
     if (p->variant > (p->precision == DBM_FP64 ? num_variants<double>() : num_variants<float>()))
         return DBM_EINVAL;
-    if (!finite_pos(p->r_in) || !std::isfinite(p->r_out) || p->r_out <= p->r_in) return DBM_EINVAL;
+    const bool disc = p->r_bc_inner == DBM_BC_CENTRE;
+    if (!(disc ? p->r_in == 0.0 : finite_pos(p->r_in)) || !std::isfinite(p->r_out) ||
+        p->r_out <= p->r_in)
+        return DBM_EINVAL;
     if (!finite_pos(p->dt) || !(p->tau > 0.0)) return DBM_EINVAL;  // tau may be +inf-like large
     if (!std::isfinite(p->Q) || !std::isfinite(p->T_th)) return DBM_EINVAL;
     if (!(p->omega1 >= 0.0) || !(p->omega2 >= 0.0) || !std::isfinite(p->omega1) ||
@@ -387,7 +403,7 @@ int dbm_check(const dbm_params *p, double *cfl)
     }
     // Courant numbers of Sec. II.C; |C_theta| is largest at the innermost radius.
     const double dr = (p->r_out - p->r_in) / p->nr;
-    const double dth = 2.0 * PI / p->ntheta;
+    const double dth = theta_span(*p) / p->ntheta;
     const double r0 = p->r_in + 0.5 * dr;
     double vmax = 0.0;
     for (int k = 0; k < 4; ++k) vmax = std::max(vmax, p->v[k]);
@@ -478,6 +494,7 @@ static int launch_init_from(dbm_t *h, const double *d_fields, cudaStream_t s)
         A.nr = h->p.nr;
         A.ntheta = h->p.ntheta;
         A.ld = h->ld;
+        A.th_over_pi = theta_span(h->p) / PI / h->p.ntheta;
         std::memcpy(A.v, h->p.v, sizeof(A.v));
         std::memcpy(A.Fc, Fc, sizeof(Fc));
         e = launch_init<double>(A, s);
@@ -490,6 +507,7 @@ static int launch_init_from(dbm_t *h, const double *d_fields, cudaStream_t s)
         A.nr = h->p.nr;
         A.ntheta = h->p.ntheta;
         A.ld = h->ld;
+        A.th_over_pi = theta_span(h->p) / PI / h->p.ntheta;
         std::memcpy(A.v, h->p.v, sizeof(A.v));
         std::memcpy(A.Fc, Fc, sizeof(Fc));
         e = launch_init<float>(A, s);
@@ -571,7 +589,8 @@ static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.ld = h->ld;
         A.r_in = p.r_in;
         A.dr = (p.r_out - p.r_in) / p.nr;
-        A.dtheta = 2.0 * PI / p.ntheta;
+        A.dtheta = theta_span(p) / p.ntheta;
+        A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
         e = launch_moments<double>(A, grid, s);
     } else {
@@ -587,7 +606,8 @@ static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.ld = h->ld;
         A.r_in = p.r_in;
         A.dr = (p.r_out - p.r_in) / p.nr;
-        A.dtheta = 2.0 * PI / p.ntheta;
+        A.dtheta = theta_span(p) / p.ntheta;
+        A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
         e = launch_moments<float>(A, grid, s);
     }
@@ -612,6 +632,7 @@ static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.nr = p.nr;
         A.ntheta = p.ntheta;
         A.ld = h->ld;
+        A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
         e = launch_noneq<double>(A, grid, s);
     } else {
@@ -623,6 +644,7 @@ static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.nr = p.nr;
         A.ntheta = p.ntheta;
         A.ld = h->ld;
+        A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
         e = launch_noneq<float>(A, grid, s);
     }

@@ -52,6 +52,8 @@ struct StepArgs {
     int items;            // strips * segs
     int reaction_energy;  // 0 explicit R, 1 consistent R
     int general_pow;      // 0: m = n = 1 (P^m = P), 1: pow()
+    int sector;           // 1: pi/4 sector, theta wrap rotates velocities by one direction
+    int centre;           // 1: disc centre at r = 0 (ghost j = -1 is j = 0 with i -> i+4)
     real cr_scale;        // dt / dr
     real ct_scale;        // dt / dtheta
     real decay;           // exp(-dt / tau)
@@ -289,15 +291,25 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     real ar[8], at[8], sa[8];
     int rn[8], tn[8];
     const int to_prev = (int)(sp - sc), to_next = (int)(sn - sc);
+    const bool wrap_prev = A.sector && m == 0;             // row -1 = last row, i -> i+1
+    const bool wrap_next = A.sector && m == A.ntheta - 1;  // row ntheta = row 0, i -> i-1
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         ar[i] = O::mul(fabs(cs[i]), A.cr_scale);
         at[i] = O::mul(O::mul(fabs(sn8[i]), A.ct_scale), inv_r);
         sa[i] = O::add(ar[i], at[i]);
         int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
-        if ((j == 0 && o < 0) || (j == A.nr - 1 && o > 0)) o = 0;  // zero-gradient ghost
+        if (j == 0 && o < 0) {
+            // inner ghost: zero-gradient, or the disc centre (same site, i -> i+4)
+            o = A.centre ? (((i + 4) & 7) - i) * WP : 0;
+        } else if (j == A.nr - 1 && o > 0) {
+            o = 0;  // zero-gradient outer ghost
+        }
         rn[i] = col + o;
-        tn[i] = col + (sn8[i] >= real(0) ? to_prev : to_next);  // C_theta >= 0: row m-1
+        if (sn8[i] >= real(0))  // C_theta >= 0: row m-1
+            tn[i] = col + to_prev + (wrap_prev ? (((i + 1) & 7) - i) * WP : 0);
+        else
+            tn[i] = col + to_next + (wrap_next ? (((i + 7) & 7) - i) * WP : 0);
     }
 
     // --- a7 + a11: update all velocities and store ------------------------
@@ -787,6 +799,7 @@ struct InitArgs {
     real *lam;
     long long plane;
     int nr, ntheta, ld;
+    double th_over_pi;  // theta_m / pi per row: 2 / ntheta, or 1 / (4 ntheta) in a sector
     double v[4];
     double Fc[4][4];
 };
@@ -815,7 +828,7 @@ __global__ void init_kernel(const InitArgs<real> A)
         const double rho = A.fields[s], ur = A.fields[N + s], uth = A.fields[2 * N + s];
         const double T = A.fields[3 * N + s], lam = A.fields[4 * N + s];
         double sth, cth;
-        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        sincospi(A.th_over_pi * m, &sth, &cth);
         const double ux = ur * cth - uth * sth, uy = ur * sth + uth * cth;
         const double u2 = ux * ux + uy * uy;
         double F[4], Fsum = 0.0;
@@ -854,6 +867,7 @@ struct MomArgs {
     long long plane;
     int nr, ntheta, ld;
     double r_in, dr, dtheta;
+    double th_over_pi;  // theta_m / pi per row
     double v[4];
 };
 
@@ -888,7 +902,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
             }
         const double T = e / rho;
         double sth, cth;
-        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        sincospi(A.th_over_pi * m, &sth, &cth);
         const double ur = ux * cth + uy * sth, uth = -ux * sth + uy * cth;
         const double lam = (double)A.lam[(long long)m * A.ld + j];
         if (A.out) {
@@ -953,7 +967,7 @@ __global__ void __launch_bounds__(256) noneq_kernel(const MomArgs<real> A)
             }
         const double ux = jx / rho, uy = jy / rho;
         double sth, cth;
-        sincospi(2.0 * m / A.ntheta, &sth, &cth);
+        sincospi(A.th_over_pi * m, &sth, &cth);
         double M[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int q = 0; q < NV; ++q) {
             const int k = q == 0 ? -1 : (q - 1) / 8, i = q == 0 ? 0 : (q - 1) % 8;

@@ -99,7 +99,7 @@ extern "C" int dbm_totals_noalloc(const dbm_params *p, const void *d_f, double *
     if (!p || !d_f || !d_totals) return DBM_EINVAL;
     if (p->nr < 1 || p->ntheta < 1 || (p->precision != DBM_FP32 && p->precision != DBM_FP64))
         return DBM_EINVAL;
-    if (!(p->r_in > 0.0) || !(p->r_out > p->r_in) || !std::isfinite(p->r_out)) return DBM_EINVAL;
+    if (!(p->r_in >= 0.0) || !(p->r_out > p->r_in) || !std::isfinite(p->r_out)) return DBM_EINVAL;
     if (p->ntheta > DBM_NOALLOC_MAX_ROWS) return DBM_ENOMEM;  // beyond the static scratch
 
     // Set-up, once per device, with that device current: the device address
@@ -122,7 +122,7 @@ extern "C" int dbm_totals_noalloc(const dbm_params *p, const void *d_f, double *
     // the scratch has to be cleared between calls.
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double dr = (p->r_out - p->r_in) / p->nr;
-    const double dth = 2.0 * kPi / p->ntheta;
+    const double dth = (p->sector ? kPi / 4.0 : 2.0 * kPi) / p->ntheta;
     if (p->precision == DBM_FP64)
         row_totals_kernel<double><<<p->ntheta, 256, 0, s>>>(static_cast<const double *>(d_f), p->nr,
                                                            p->ntheta, p->r_in, dr, dth, p->v[0],

@@ -18,7 +18,7 @@ NV = 33
 DBM_OK, DBM_EINVAL, DBM_ECFL, DBM_ENOMEM, DBM_EBUSY, DBM_ENOTREADY = 0, 1, 2, 3, 4, 5
 DBM_ETIMEOUT, DBM_ENONFINITE, DBM_ECUDA, DBM_ECANCELLED, DBM_ENOTFOUND = 6, 7, 8, 9, 10
 DBM_FP32, DBM_FP64 = 0, 1
-DBM_BC_OUTFLOW = 0
+DBM_BC_OUTFLOW, DBM_BC_CENTRE = 0, 1
 DBM_R_EXPLICIT, DBM_R_CONSISTENT = 0, 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -31,6 +31,7 @@ class DbmParams(ctypes.Structure):
         ("precision", ctypes.c_int32), ("reaction_energy", ctypes.c_int32),
         ("r_bc_inner", ctypes.c_int32), ("r_bc_outer", ctypes.c_int32),
         ("rows_per_item", ctypes.c_int32), ("variant", ctypes.c_int32),
+        ("sector", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
         ("dt", ctypes.c_double), ("tau", ctypes.c_double),
         ("Q", ctypes.c_double), ("omega1", ctypes.c_double), ("omega2", ctypes.c_double),
@@ -319,6 +320,8 @@ def params_from(d: dict) -> DbmParams:
     p.reaction_energy = _RE[d.get("reaction_energy", 0)]
     p.rows_per_item = int(d.get("rows_per_item", 0))
     p.variant = int(d.get("variant", 0))
+    p.sector = int(d.get("sector", 0))
+    p.r_bc_inner = {"outflow": DBM_BC_OUTFLOW, "centre": DBM_BC_CENTRE, 0: 0, 1: 1}[d.get("r_bc_inner", 0)]
     return p
 
 

@@ -69,11 +69,12 @@ class Workload:
         return int(self.params["nr"]) * int(self.params["ntheta"])
 
 
-def grid(nr: int, ntheta: int, r_in: float, r_out: float):
-    """(r, theta) broadcast grids of shape (ntheta, nr)."""
+def grid(nr: int, ntheta: int, r_in: float, r_out: float, sector: int = 0):
+    """(r, theta) broadcast grids of shape (ntheta, nr) (theta span 2 pi, or
+    pi/4 for a sector)."""
     dr = (r_out - r_in) / nr
     r = r_in + (np.arange(nr) + 0.5) * dr
-    th = np.arange(ntheta) * (2.0 * math.pi / ntheta)
+    th = np.arange(ntheta) * ((math.pi / 4 if sector else 2.0 * math.pi) / ntheta)
     return np.broadcast_to(r[None, :], (ntheta, nr)), np.broadcast_to(th[:, None], (ntheta, nr))
 
 
@@ -84,8 +85,8 @@ def base_params(**kw) -> dict:
     return p
 
 
-def _two_state(nr, ntheta, r_in, r_out, inside, state_in, state_out):
-    r, th = grid(nr, ntheta, r_in, r_out)
+def _two_state(nr, ntheta, r_in, r_out, inside, state_in, state_out, sector=0):
+    r, th = grid(nr, ntheta, r_in, r_out, sector)
     mask = inside(r, th)
     out = {}
     for i, name in enumerate(("rho", "ur", "uth", "T", "lam")):
@@ -159,7 +160,7 @@ def uniform_state(nr: int, ntheta: int, rho: float, ux: float, uy: float, T: flo
     """A spatially uniform state with Cartesian velocity (ux, uy): its polar
     components vary with theta as u_r = ux cos + uy sin, u_th = -ux sin + uy cos."""
     p = base_params(nr=nr, ntheta=ntheta, **kw)
-    r, th = grid(nr, ntheta, p["r_in"], p["r_out"])
+    r, th = grid(nr, ntheta, p["r_in"], p["r_out"], p.get("sector", 0))
     f = dict(rho=np.full((ntheta, nr), float(rho)),
              ur=ux * np.cos(th) + uy * np.sin(th),
              uth=-ux * np.sin(th) + uy * np.cos(th),
@@ -173,7 +174,7 @@ def random_smooth(nr: int, ntheta: int, seed: int = 0, amp: float = 0.1, **kw) -
     """Smooth random fields (a few seeded Fourier modes in r and theta) around
     rho = 1, T = 1.3, u = 0, lambda = 0.3, for parity tests of every term."""
     p = base_params(nr=nr, ntheta=ntheta, **kw)
-    r, th = grid(nr, ntheta, p["r_in"], p["r_out"])
+    r, th = grid(nr, ntheta, p["r_in"], p["r_out"], p.get("sector", 0))
     x = (r - p["r_in"]) / (p["r_out"] - p["r_in"])
     out = {}
     base = dict(rho=1.0, ur=0.0, uth=0.0, T=1.3, lam=0.3)
@@ -253,3 +254,33 @@ def serving_request(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
         w = implosion(N, N, steps, seed=seed + k, omega1=w1, dt=dt)
     w.name = f"req{k}_{w.name}"
     return w
+
+
+def paper_explosion(R1: float, R: float, nr: int, dt: float = 1.25e-6, nsteps: int = 0,
+                    precision: str = "fp32") -> Workload:
+    """The paper's explosion runs (Sec. III.D): a disc of radius R in one pi/4
+    sector cell (ntheta = 1) with the centre rule; reacted driver (rho, T,
+    u_r, u_theta, lambda) = (1.5, 1.55556, 0.666667, 0, 1) for r <= R1 into
+    (1, 1, 0, 0, 0); tau 2e-4, omega1 1, omega2 50.  The paper's cases are
+    (R1, R, nr) = (0.015, 0.3, 6000), (0.023, 0.75, 15000), (0.05, 1.2, 24000)
+    with dt 2.5e-6; dt defaults to half of that (Courant sum <= 1 at the
+    innermost cell)."""
+    p = base_params(nr=nr, ntheta=1, r_in=0.0, r_out=R, dt=dt, tau=2e-4, omega1=1.0,
+                    omega2=50.0, precision=precision, sector=1, r_bc_inner="centre")
+    f = _two_state(nr, 1, 0.0, R, lambda r, th: r <= R1,
+                   (1.5, 0.666667, 0.0, 1.55556, 1.0), (1.0, 0.0, 0.0, 1.0, 0.0))
+    return Workload(f"paper_explosion_R1_{R1}", p, f, nsteps, dict(R1=R1, R=R))
+
+
+def paper_implosion(nr: int = 2000, dt: float = 1.25e-6, nsteps: int = 0,
+                    precision: str = "fp32") -> Workload:
+    """The paper's implosion run (Sec. III.C): disc of radius 0.1, one pi/4
+    sector cell, centre rule; shocked reacted ring (1.5, 1.55556, -0.666667,
+    0, 1) for 0.098 < r <= 0.1 driving into (1, 1, 0, 0, 0); tau 2e-4,
+    omega1 1, omega2 50; the paper's nr = 2000 with dt 2.5e-6 (default here
+    half of that)."""
+    p = base_params(nr=nr, ntheta=1, r_in=0.0, r_out=0.1, dt=dt, tau=2e-4, omega1=1.0,
+                    omega2=50.0, precision=precision, sector=1, r_bc_inner="centre")
+    f = _two_state(nr, 1, 0.0, 0.1, lambda r, th: r > 0.098,
+                   (1.5, -0.666667, 0.0, 1.55556, 1.0), (1.0, 0.0, 0.0, 1.0, 0.0))
+    return Workload("paper_implosion", p, f, nsteps)

@@ -7,6 +7,7 @@ max(|u_r|, |u_theta|) for both velocity components (they vanish in places),
 floored at 1e-3 of the thermal speed sqrt(max T) (a state at rest has u = 0).
 """
 import hashlib
+import json
 
 import numpy as np
 
@@ -71,6 +72,8 @@ def run_oracle(orc, w, nsteps=None, **overrides):
 
 def assert_close(gpu, ref, tol, label=""):
     errs = rel_errors(gpu, ref)
+    # one line per comparison, collected into the accuracy table from `pytest -s`
+    print("ACCURACY", json.dumps({"case": label, "tol": tol, "errors": errs}))
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, f"{label}: relative L-inf above {tol}: {bad} (all: {errs})"
     return errs

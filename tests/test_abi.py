@@ -71,7 +71,8 @@ def test_check_reports_the_courant_number():
                                          ("dt", 0.0), ("tau", 0.0), ("omega1", -1.0),
                                          ("precision", 7), ("reaction_energy", 3),
                                          ("rows_per_item", -2), ("variant", 99),
-                                         ("variant", -1)])
+                                         ("variant", -1), ("sector", 2), ("reserved", 1),
+                                         ("r_bc_inner", 1), ("r_bc_outer", 1), ("r_bc_inner", 7)])
 def test_check_rejects_invalid_parameters(field, value):
     p = dbm.dbm_params_default()
     setattr(p, field, value)

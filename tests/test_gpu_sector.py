@@ -1,0 +1,114 @@
+"""Sector and disc-centre geometry on the GPU (Sec. II.D): parity with the
+oracle, and the paper's own disc runs (Sec. III.C-D): the disc centre stays
+in equilibrium during the implosion, a small ignition ring (R1 = 0.015) dies
+out while a large one (R1 = 0.05) detonates."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL, assert_close, run_gpu, run_oracle
+from paper_1308_0653_gb300 import dbm
+from paper_1308_0653_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _sector_workload(nr, nth, disc, seed):
+    r_in = 0.0 if disc else 0.3
+    w = W.random_smooth(nr, nth, seed=seed, amp=0.12, r_in=r_in, r_out=1.3, omega1=3.0,
+                        omega2=4.0, tau=5e-4, sector=1, r_bc_inner="centre" if disc else "outflow")
+    dr = (1.3 - r_in) / nr
+    w.params["dt"] = 0.35 * min(dr, (r_in + dr / 2) * math.pi / 4 / nth) / 12.5
+    w.fields["T"] = w.fields["T"] * 0.9
+    return w
+
+
+@pytest.mark.parametrize("disc", [False, True])
+@pytest.mark.parametrize("nr,nth", [(40, 1), (150, 3), (64, 16)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sector_and_disc_match_the_oracle(orc, disc, nr, nth, precision):
+    w = _sector_workload(nr, nth, disc, seed=nr + nth + int(disc))
+    ref = run_oracle(orc, w, nsteps=60, sector=1, r_bc_inner=1 if disc else 0)
+    out = run_gpu(w, precision, nsteps=60)
+    assert_close(out, ref, TOL[precision], f"sector nr={nr} nth={nth} disc={disc} {precision}")
+
+
+def test_invalid_disc_configurations_are_rejected():
+    p = dbm.dbm_params_default()
+    p.r_bc_inner = dbm.DBM_BC_CENTRE
+    p.r_in = 0.0
+    assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL   # centre needs a sector
+    p.sector = 1
+    p.dt = 1e-7
+    assert dbm.dbm_check(p)[0] == dbm.DBM_OK
+    p.r_in = 0.01
+    assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL   # centre needs r_in = 0
+
+
+def _run_paper(w, times, dt):
+    sim = dbm.Simulation(dict(w.params, precision="fp32"))
+    sim.init_state(w.fields)
+    out, t_prev = [], 0.0
+    for t in times:
+        sim.step(int(round((t - t_prev) / dt)))
+        t_prev = t
+        m = sim.moments()
+        m["noneq"] = sim.noneq()
+        out.append(m)
+    sim.close()
+    return out
+
+
+def test_paper_implosion_centre_stays_in_equilibrium():
+    """Sec. III.C: the inward detonation compresses the centre (density,
+    temperature and pressure peak there) while the gas at the disc centre
+    stays in thermodynamic equilibrium (Delta*_{2,rr} ~ 0 there)."""
+    dt = 1.25e-6
+    w = W.paper_implosion(nr=2000, dt=dt)
+    snaps = _run_paper(w, [0.0375, 0.0425, 0.05], dt)
+    peak_rho = max(s["rho"].max() for s in snaps)
+    assert peak_rho > 2.0
+    for s in snaps:
+        d2 = s["noneq"][0, 0]
+        assert np.isfinite(d2).all()
+        assert abs(d2[0]) < 0.05 * np.abs(d2).max()
+        np.testing.assert_allclose(s["ur"][0, 0], 0.0, atol=0.05)
+
+
+def test_paper_explosion_small_ring_dies_out():
+    """Sec. III.D, Fig. 7: with R1 = 0.015 the released energy cannot keep up
+    with the geometric divergence; lambda changes only near the start and the
+    disturbance decays (no reaction front out in the fresh gas)."""
+    dt = 1.25e-6
+    w = W.paper_explosion(0.015, 0.3, 6000, dt=dt)
+    r = (np.arange(6000) + 0.5) * 0.3 / 6000
+    (s,) = _run_paper(w, [0.15], dt)
+    assert s["lam"][0, r > 0.05].max() < 0.05
+    assert (s["rho"][0] * s["T"][0]).max() < 1.3
+
+
+def test_paper_explosion_large_ring_detonates():
+    """Sec. III.D, Fig. 9: with R1 = 0.05 the ignition energy is large enough
+    for a direct detonation: a burnt region (lambda ~ 1) behind a strong
+    pressure front that has moved far out by t = 0.25 (to r = 0.47 here)."""
+    dt = 1.25e-6
+    w = W.paper_explosion(0.05, 1.2, 24000, dt=dt)
+    r = (np.arange(24000) + 0.5) * 1.2 / 24000
+    (s,) = _run_paper(w, [0.25], dt)
+    lam = s["lam"][0]
+    front = r[np.nonzero(lam > 0.5)[0].max()]
+    print("large ring: lambda = 1/2 front at", front, "max P", (s["rho"][0] * s["T"][0]).max())
+    # the burnt region reaches far into the fresh gas (the small ring's
+    # reaction never leaves r < 0.05) and stays fully burnt behind the front
+    assert front > 0.3
+    assert lam[(r > 0.1) & (r < front - 0.05)].min() > 0.99
+    assert (s["rho"][0] * s["T"][0]).max() > 3.0
