@@ -296,8 +296,12 @@ def run_ours(args):
     alg_bytes = BYTES_PER_SITE["fp32"] * sites
     achieved = alg_bytes / per_launch / 1e9
     peak, peak_src = measured_peak()
-    kname = {1: "dbm::step_kernel<float,128,6> (v1)", 2: "dbm::step_kernel_v2<float,128,6,false,2>",
-             3: "dbm::step_kernel_v2<float,128,4,true,3>"}.get(launch["variant"], f"variant {launch['variant']}")
+    kname = {1: "dbm::step_kernel<float,128,6> (v1, row barrier)",
+             2: "dbm::step_kernel_v2<float,128,6,false,2,false> (bulk copies)",
+             3: "dbm::step_kernel_v2<float,128,4,true,3,false> (bulk copies)",
+             4: "dbm::step_kernel_v2<float,128,6,false,2,true> (tensor-map TMA)",
+             5: "dbm::step_kernel_v2<float,128,4,true,3,true> (tensor-map TMA)"}.get(
+                 launch["variant"], f"variant {launch['variant']}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None, "kernel": kname,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch * 1e3,

@@ -2,6 +2,8 @@
 // (declarations and contracts in include/dbm.h).  Host code only: it
 // validates parameters, carves the caller's device buffer, builds the
 // geometry tables, picks the launch configuration and enqueues kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -136,11 +138,55 @@ struct dbm_s {
     StepArgs<double> a64[2];
     cudaGraphExec_t graph;    // GRAPH_STEPS steps starting from buffer 0
     int device;
+    bool tmap_ok;             // tensor maps encoded (tensor-TMA variants usable)
 };
 
 namespace {
 
 constexpr int GRAPH_STEPS = 32;
+
+// cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor maps of one parity's inputs: f as (ld, ntheta, 33) and lambda as
+// (ld, ntheta), box = one row of W + 2 halo columns (all 33 planes for f).
+template <typename real>
+bool encode_maps(const dbm_t *h, StepArgs<real> &A)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt =
+        sizeof(real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t e = sizeof(real);
+    const cuuint32_t bx = (cuuint32_t)(h->ki.W + 2 * h->ki.halo);
+    const cuuint64_t gdim3[3] = {(cuuint64_t)h->ld, (cuuint64_t)h->p.ntheta, (cuuint64_t)NV};
+    const cuuint64_t gstr3[2] = {(cuuint64_t)h->ld * e, (cuuint64_t)h->ld * h->p.ntheta * e};
+    const cuuint32_t box3[3] = {bx, 1, (cuuint32_t)NV};
+    const cuuint32_t one3[3] = {1, 1, 1};
+    if (enc(&A.tm_f, dt, 3, (void *)A.f_in, gdim3, gstr3, box3, one3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t gdim2[2] = {(cuuint64_t)h->ld, (cuuint64_t)h->p.ntheta};
+    const cuuint64_t gstr2[1] = {(cuuint64_t)h->ld * e};
+    const cuuint32_t box2[2] = {bx, 1};
+    return enc(&A.tm_lam, dt, 2, (void *)A.lam_in, gdim2, gstr2, box2, one3, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 template <typename real>
 void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
@@ -190,6 +236,7 @@ void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
             for (int c = 0; c < 4; ++c) A.Fc[k][c] = (real)Fc[k][c];
         }
     }
+    h->tmap_ok = encode_maps(h, a[0]) && encode_maps(h, a[1]);
 }
 
 template <typename real>
@@ -301,11 +348,28 @@ int configure_launch(dbm_t *h, int variant)
         L_rows = (int)std::max(1LL, need);
     }
     L_rows = std::min(L_rows, p.ntheta);
+    const KernelInfo old_ki = h->ki;
     h->ki = ki;
+    if (p.precision == DBM_FP64)
+        fill_step_args<double>(h, h->a64);
+    else
+        fill_step_args<float>(h, h->a32);
+    if (ki.version == 3 && !h->tmap_ok) {  // tensor maps not encodable for this grid
+        h->ki = old_ki;
+        if (old_ki.W) {
+            if (p.precision == DBM_FP64)
+                fill_step_args<double>(h, h->a64);
+            else
+                fill_step_args<float>(h, h->a32);
+        }
+        snprintf(g_last_error, sizeof(g_last_error), "variant %d needs tensor maps, not available here", variant);
+        return DBM_EINVAL;
+    }
     h->variant = variant;
     h->rows_per_item = L_rows;
     h->items = strips * ((p.ntheta + L_rows - 1) / L_rows);
     h->grid = std::min(h->items, slots);
+    // the step arguments carry the launch shape too
     if (p.precision == DBM_FP64)
         fill_step_args<double>(h, h->a64);
     else
@@ -793,8 +857,10 @@ int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_ste
     float bestms = 0.f;
     int rc = DBM_OK;
     for (int v = 1; v <= nv && rc == DBM_OK; ++v) {
-        rc = configure_launch(h, v);
-        if (rc != DBM_OK) break;
+        if (configure_launch(h, v) != DBM_OK) {  // not available for this grid
+            if (ms_per_step) ms_per_step[v - 1] = 0.f;
+            continue;
+        }
         // two untimed steps, then `steps` timed single launches
         for (int k = 0; k < 2 && rc == DBM_OK; ++k) {
             rc = launch_one(h, h->cur, s);

@@ -18,6 +18,7 @@
 // item) and written once.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; descriptors are encoded by the host runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,14 +30,20 @@ constexpr int NARR = 34;  // 33 f planes + lambda
 // Status bits written by kernels into the instance's status word.
 constexpr int ST_WAIT_TIMEOUT = 1;   // an mbarrier wait gave up
 constexpr int ST_NONFINITE = 2;      // a moment was NaN / inf (moments kernel)
+constexpr int ST_SMEM_ALIGN = 4;     // dynamic shared memory not 128-byte aligned (step skipped)
 
 template <typename real> struct Halo;
 template <> struct Halo<float> { static constexpr int value = 4; };   // 16 bytes
 template <> struct Halo<double> { static constexpr int value = 2; };  // 16 bytes
 
 // Per-instance constants of the step (host-computed in double, rounded to real).
+// The tensor maps describe this parity's input f as a 3-D tensor (ld, ntheta,
+// 33) and lambda as 2-D (ld, ntheta), with a box of one row of W + 2 HALO
+// columns; they are used by the tensor-TMA variants.
 template <typename real>
 struct StepArgs {
+    CUtensorMap tm_f;     // 128 B, 64-byte aligned
+    CUtensorMap tm_lam;
     const real *f_in;
     real *f_out;
     const real *lam_in;
@@ -130,6 +137,27 @@ __device__ __forceinline__ void named_bar_sync(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Tensor TMA: tile of a 3-D / 2-D tensor map at coordinates (x, y[, z]),
+// x innermost; out-of-range elements are filled with zeros.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -190,7 +218,7 @@ template <> struct Op<double> {
 // moments and equilibrium use the fixed direction cosines; its polar Courant
 // numbers use the row's c_i = cos(i pi/4 - theta_m), s_i = sin(...).
 // ---------------------------------------------------------------------------
-template <typename real, int WP, bool REREAD = false>
+template <typename real, int WP, bool REREAD = false, int LAMOFF = NV * WP>
 __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real *__restrict__ sp,
                                             const real *__restrict__ sc,
                                             const real *__restrict__ sn, int col, int j, int m,
@@ -204,7 +232,7 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     real f[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) f[q] = sc[q * WP + col];
-    const real lam = sc[NV * WP + col];
+    const real lam = sc[LAMOFF + col];
 
     // --- a2: moments, ring by ring (Cartesian components) ------------------
     //     rho = sum f, rho u = sum f v, e2 = sum f v^2, T = (e2/rho - u^2)/2
@@ -345,8 +373,8 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     const real uth = O::fma(uy, cth, -O::mul(ux, sth));
     int orr = ur >= real(0) ? -1 : 1;
     if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
-    const real lr = sc[NV * WP + col + orr];
-    const real lt = (uth >= real(0) ? sp : sn)[NV * WP + col];
+    const real lr = sc[LAMOFF + col + orr];
+    const real lt = (uth >= real(0) ? sp : sn)[LAMOFF + col];
     real ln = O::add(lam, dlam);
     ln = O::sub(ln, O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lam, lr)));
     ln = O::sub(ln, O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lam, lt)));
@@ -586,6 +614,16 @@ static __global__ void batch_advance_kernel(long long *T, int k)
     if (threadIdx.x == 0 && blockIdx.x == 0) *T += k;
 }
 
+// Row-buffer layout of the v2 pipeline (in elements of real).
+template <typename real, int W>
+struct V2Layout {
+    static constexpr int wp = W + 2 * Halo<real>::value;
+    static constexpr int a128 = 128 / (int)sizeof(real);
+    static constexpr int lam = (NV * wp + a128 - 1) / a128 * a128;  // 128-byte aligned
+    static constexpr int tab = lam + wp;                            // 16 trig values
+    static constexpr int slot = (tab + 16 + a128 - 1) / a128 * a128;
+};
+
 // ---------------------------------------------------------------------------
 // v2 pipeline: warp-specialised.  Warp W/32 is the producer: it issues the
 // TMA bulk copies of each row (34 arrays + the row's 16 trig values) into a
@@ -597,17 +635,24 @@ static __global__ void batch_advance_kernel(long long *T, int k)
 // for the slowest.  Positions are released after their last use: after
 // centre P the buffer of P-1, and at an item's last centre also P and P+1.
 // ---------------------------------------------------------------------------
-template <typename real, int W, int NSTAGE, bool REREAD, typename Work>
+template <typename real, int W, int NSTAGE, bool REREAD, bool TMAP, typename Work>
 __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw,
                                        StepArgs<real> *sargs2)
 {
     constexpr int HALO = Halo<real>::value;
     constexpr int WP = W + 2 * HALO;
     constexpr int TAB = 16;
-    constexpr int SLOT = NARR * WP + TAB;  // elements per row buffer (trig values last)
     constexpr int NCW = W / 32;            // consumer warps
+    // Row buffer layout (elements): 33 f rows of WP, then lambda at the next
+    // 128-byte boundary (tensor-TMA destinations must be 128-byte aligned),
+    // then the 16 trig values; the buffer size is a multiple of 128 bytes.
+    constexpr int LAMOFF = V2Layout<real, W>::lam;
+    constexpr int RTOFF = V2Layout<real, W>::tab;
+    constexpr int SLOT = V2Layout<real, W>::slot;
     static_assert(NSTAGE >= 3, "rows m-1, m, m+1 must be resident");
-    static_assert((SLOT * sizeof(real)) % 16 == 0, "row buffers must stay 16-byte aligned");
+    static_assert((SLOT * sizeof(real)) % 128 == 0, "row buffers must be 128-byte aligned");
+    static_assert((LAMOFF * sizeof(real)) % 128 == 0, "lambda tile must be 128-byte aligned");
+    static_assert((RTOFF * sizeof(real)) % 16 == 0, "trig row must be 16-byte aligned");
 
     real *sm = reinterpret_cast<real *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + sizeof(real) * NSTAGE * SLOT);
@@ -629,6 +674,18 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         issued_total = 0;
     }
     __syncthreads();
+    if ((smem_addr(smem_raw) & 127u) != 0u) {  // layout assumption broken: report, copy nothing
+        if (tx == 0 && nitems > 0) {
+            const StepArgs<real> *a;
+            int j0, mb, me;
+            for (int it = blockIdx.x; it < nitems; it += gridDim.x)
+                if (work.item(it, a, j0, mb, me)) {
+                    atomicOr(a->status, ST_SMEM_ALIGN);
+                    break;
+                }
+        }
+        return;
+    }
 
     if (warp == NCW) {
         // ------------------------------ producer ------------------------------
@@ -661,20 +718,34 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
             int m = pmb - 1 + p_row;
             const int nth = pa->ntheta;
             m = m < 0 ? m + nth : (m >= nth ? m - nth : m);
-            const int jlo = max(pj0 - HALO, 0);
-            const int jhi = min(pj0 + W + HALO, pa->ld);
-            const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
             real *buf = sm + slot * SLOT;
-            real *dst = buf + (jlo - (pj0 - HALO));
-            if (lane == 0) mbar_arrive_expect_tx(&full[slot], nbytes * NARR + TAB * (uint32_t)sizeof(real));
-            __syncwarp();
-            fence_proxy_async_smem();
-            const long long roff = (long long)m * pa->ld + jlo;
-            for (int a = lane; a < NARR; a += 32) {
-                const real *src = (a < NV) ? pa->f_in + (long long)a * pa->plane + roff : pa->lam_in + roff;
-                bulk_g2s(dst + a * WP, src, nbytes, &full[slot]);
+            if constexpr (TMAP) {
+                // one 3-D tile (all 33 f planes of the strip's row), one 2-D tile
+                // (lambda), one bulk copy (trig row); the box starts at the
+                // halo column pj0 - HALO and out-of-range columns are zeros
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[slot], (uint32_t)(WP * NARR + TAB) * (uint32_t)sizeof(real));  // 33 + 1 rows + trig
+                    fence_proxy_async_smem();
+                    tma_load_3d(buf, &pa->tm_f, pj0 - HALO, m, 0, &full[slot]);
+                    tma_load_2d(buf + LAMOFF, &pa->tm_lam, pj0 - HALO, m, &full[slot]);
+                    bulk_g2s(buf + RTOFF, pa->rowtab + (long long)m * TAB, TAB * sizeof(real), &full[slot]);
+                }
+                __syncwarp();
+            } else {
+                const int jlo = max(pj0 - HALO, 0);
+                const int jhi = min(pj0 + W + HALO, pa->ld);
+                const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
+                real *dst = buf + (jlo - (pj0 - HALO));
+                if (lane == 0) mbar_arrive_expect_tx(&full[slot], nbytes * NARR + TAB * (uint32_t)sizeof(real));
+                __syncwarp();
+                fence_proxy_async_smem();
+                const long long roff = (long long)m * pa->ld + jlo;
+                for (int a = lane; a < NARR; a += 32) {
+                    const real *src = (a < NV) ? pa->f_in + (long long)a * pa->plane + roff : pa->lam_in + roff;
+                    bulk_g2s(a < NV ? dst + a * WP : dst + LAMOFF, src, nbytes, &full[slot]);
+                }
+                if (lane == 31) bulk_g2s(buf + RTOFF, pa->rowtab + (long long)m * TAB, TAB * sizeof(real), &full[slot]);
             }
-            if (lane == 31) bulk_g2s(buf + NARR * WP, pa->rowtab + (long long)m * TAB, TAB * sizeof(real), &full[slot]);
             ++issued;
             if (++p_row == (pme - pmb) + 2) {
                 p_row = 0;
@@ -725,13 +796,13 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 const real *sc = sm + (P % NSTAGE) * SLOT;
                 if (active) {
                     real cs[8], sn8[8];
-                    const real *rt = sc + NARR * WP;
+                    const real *rt = sc + RTOFF;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         cs[i] = rt[i];
                         sn8[i] = rt[8 + i];
                     }
-                    site_update<real, WP, REREAD>(A, sm + ((P - 1) % NSTAGE) * SLOT, sc,
+                    site_update<real, WP, REREAD, LAMOFF>(A, sm + ((P - 1) % NSTAGE) * SLOT, sc,
                                                   sm + ((P + 1) % NSTAGE) * SLOT, HALO + tx, j,
                                                   mb + c - 1, inv_r, cs, sn8);
                 }
@@ -756,27 +827,27 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
     }
 }
 
-template <typename real, int W, int NSTAGE, bool REREAD, int MINB>
+template <typename real, int W, int NSTAGE, bool REREAD, int MINB, bool TMAP>
 __global__ void __launch_bounds__(W + 32, MINB) step_kernel_v2(const __grid_constant__ StepArgs<real> A)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SingleWork<real, W> work{&A};
-    march2<real, W, NSTAGE, REREAD>(work, smem_raw, nullptr);
+    march2<real, W, NSTAGE, REREAD, TMAP>(work, smem_raw, nullptr);
 }
 
-template <typename real, int W, int NSTAGE, bool REREAD, int MINB>
+template <typename real, int W, int NSTAGE, bool REREAD, int MINB, bool TMAP>
 __global__ void __launch_bounds__(W + 32, MINB) batch_step_kernel_v2(const __grid_constant__ BatchArgs<real> B)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(16) StepArgs<real> sargs2[2];
+    __shared__ __align__(64) StepArgs<real> sargs2[2];
     BatchWork<real, W> work{B.slots, B.items, *B.n_items, *B.T + B.s};
-    march2<real, W, NSTAGE, REREAD>(work, smem_raw, sargs2);
+    march2<real, W, NSTAGE, REREAD, TMAP>(work, smem_raw, sargs2);
 }
 
 template <typename real, int W, int NSTAGE>
 constexpr int smem_bytes_v2()
 {
-    return (int)(sizeof(real) * NSTAGE * (NARR * (W + 2 * Halo<real>::value) + 16) + 16 * NSTAGE);
+    return (int)(sizeof(real) * NSTAGE * V2Layout<real, W>::slot + 16 * NSTAGE);
 }
 
 // Self-test of Op<float>::rcp against the correctly rounded division.

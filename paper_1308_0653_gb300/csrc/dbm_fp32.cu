@@ -3,8 +3,11 @@
 //   1  v1  128  6  no   2   CTA-wide barrier per row (111 KB shared)
 //   2  v2  128  6  no   2   producer warp + full/empty mbarriers (111 KB)
 //   3  v2  128  4  yes  3   as 2 with a 4-deep ring (74 KB) and <= 136 registers
+//   4  v3  128  6  no   2   as 2, rows loaded by tensor-map TMA (3 copies per row)
+//   5  v3  128  4  yes  3   as 3, rows loaded by tensor-map TMA
 #define DBM_REAL float
-#define DBM_VARIANTS(X) X(1, 1, 128, 6, false, 2) X(2, 2, 128, 6, false, 2) X(3, 2, 128, 4, true, 3)
+#define DBM_VARIANTS(X) X(1, 1, 128, 6, false, 2) X(2, 2, 128, 6, false, 2) X(3, 2, 128, 4, true, 3) \
+    X(4, 3, 128, 6, false, 2) X(5, 3, 128, 4, true, 3)
 #define DBM_DEFAULT_VARIANT 2
 #include "dbm_launch_impl.cuh"
 

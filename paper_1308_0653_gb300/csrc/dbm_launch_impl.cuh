@@ -1,6 +1,8 @@
 // Instantiates the kernels of one precision; included once per precision
 // translation unit with DBM_REAL and the variant list DBM_VARIANTS(X) defined,
 // X(id, version, W, NSTAGE, REREAD, MIN_BLOCKS_PER_SM), and DBM_DEFAULT_VARIANT.
+// version 1: CTA-wide row barrier; 2: producer warp, per-array bulk copies;
+// 3: producer warp, tensor-map TMA tiles.
 #include "dbm_launch.h"
 
 namespace dbm {
@@ -26,21 +28,27 @@ struct Variant<1, W, NS, RR, MB> {
     }
 };
 
-template <int W, int NS, bool RR, int MB>
-struct Variant<2, W, NS, RR, MB> {
+template <int W, int NS, bool RR, int MB, bool TM>
+struct VariantV2 {
     static constexpr int kThreads = W + 32;
     static constexpr int kSmem = smem_bytes_v2<DBM_REAL, W, NS>();
-    static void *single() { return (void *)step_kernel_v2<DBM_REAL, W, NS, RR, MB>; }
-    static void *batch() { return (void *)batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB>; }
+    static void *single() { return (void *)step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM>; }
+    static void *batch() { return (void *)batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM>; }
     static void run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
     {
-        step_kernel_v2<DBM_REAL, W, NS, RR, MB><<<g, kThreads, kSmem, s>>>(A);
+        step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM><<<g, kThreads, kSmem, s>>>(A);
     }
     static void run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
     {
-        batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB><<<g, kThreads, kSmem, s>>>(B);
+        batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM><<<g, kThreads, kSmem, s>>>(B);
     }
 };
+
+template <int W, int NS, bool RR, int MB>
+struct Variant<2, W, NS, RR, MB> : VariantV2<W, NS, RR, MB, false> {};
+
+template <int W, int NS, bool RR, int MB>
+struct Variant<3, W, NS, RR, MB> : VariantV2<W, NS, RR, MB, true> {};
 
 template <typename V>
 cudaError_t info_of(void *fn, int ver, int W, int NS, KernelInfo *out)
