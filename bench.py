@@ -38,6 +38,30 @@ NV = 33
 BYTES_PER_SITE = {"fp32": 33 * 4 * 2 + 4 * 2, "fp64": 33 * 8 * 2 + 8 * 2}  # f + lambda, read + write
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM traffic of the FP32 step kernel measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch, one-pass capture of the bench workload; the
+# summary with its command is in profiles/).  A capture counts only while the
+# kernel and launch sources still hash to the value it was taken with.
+KERNEL_SOURCES = ("dbm_device.cuh", "dbm_launch.h", "dbm_launch_impl.cuh", "dbm_fp32.cu", "dbm_api.cu")
+TRAFFIC_CAPTURES = []  # dicts: variant, nr, ntheta, bytes, sources_sha256
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1308_0653_gb300", "csrc", name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(variant, nr, ntheta):
+    sha = kernel_sources_sha256()
+    for c in TRAFFIC_CAPTURES:
+        if (c["variant"], c["nr"], c["ntheta"]) == (variant, nr, ntheta) and c["sources_sha256"] == sha:
+            return c["bytes"]
+    return None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -51,7 +75,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=40)
     ap.add_argument("--variant", type=int, default=0,
-                    help="step-kernel variant; 0 = autotune on a separate handle first")
+                    help="step-kernel variant; 0 = the library's choice for this size")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every variant on a separate handle first and run the fastest")
     ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
                     help="step: the default line; batch: 64 uneven instances in one persistent "
                          "launch per step; serve: Poisson arrivals through dbm_submit/dbm_poll")
@@ -256,7 +282,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     tune = None
-    if args.variant == 0:
+    if args.variant == 0 and args.autotune:
         # autotuner: time every kernel variant on a separate handle of the same
         # size; the choice is remembered for this size class (used below)
         t = dbm.Simulation(dict(w.params, precision="fp32"), device=dev)
@@ -303,7 +329,9 @@ def run_ours(args):
              5: "dbm::step_kernel_v2<float,128,4,true,3,true> (tensor-map TMA)"}.get(
                  launch["variant"], f"variant {launch['variant']}")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": kname,
+            "frac": achieved / peak, "traffic": measured_traffic(launch["variant"], w.params["nr"],
+                                                                 w.params["ntheta"]),
+            "kernel": kname,
             "algorithmic_bytes_per_launch": alg_bytes, "launch_ms": per_launch * 1e3,
             "peak_source": peak_src}
     sim.close()

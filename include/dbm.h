@@ -311,16 +311,21 @@ int64_t dbm_batch_remaining(const dbm_batch_t *b, int slot);
 int64_t dbm_batch_time(const dbm_batch_t *b);
 
 /* Upload the slot and item tables (stream-ordered; done automatically by
- * dbm_batch_step after attach/detach).  Errors: DBM_ENOMEM (more items than
- * max_items), DBM_ECUDA. */
+ * dbm_batch_step after attach/detach) and pick the batch kernel: the
+ * precision's default (tensor-map row loads for FP32) when every attached
+ * simulation has usable tensor maps, else the bulk-copy variant.  A change of
+ * kernel waits for `stream` to drain and drops the captured step graph.
+ * Errors: DBM_ENOMEM (more items than max_items), DBM_ECUDA. */
 int dbm_batch_commit(dbm_batch_t *b, void *stream);
 
 /* Advance the step counter nsteps steps on `stream` (asynchronous); every
  * attached simulation advances while it has steps left. */
 int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
 
-/* Launch shape: persistent grid, current number of work items, rows per item. */
-int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item);
+/* Launch shape: persistent grid, current number of work items, rows per item,
+ * kernel variant (as of the last commit).  Null outputs are skipped. */
+int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item,
+                          int *variant);
 
 /* ---- serving: continuous batching behind submit / poll ------------------ */
 /*

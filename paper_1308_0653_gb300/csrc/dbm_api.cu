@@ -516,7 +516,12 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
         delete h;
         return cuda_fail(e, "dbm_create: device query");
     }
-    rc = configure_launch(h, pick_variant(*p));
+    const int v0 = pick_variant(*p);
+    rc = configure_launch(h, v0);
+    if (rc != DBM_OK && p->variant == 0) {  // chosen, not asked for: fall back to bulk copies
+        const int fb = p->precision == DBM_FP64 ? fallback_variant<double>() : fallback_variant<float>();
+        if (fb != v0) rc = configure_launch(h, fb);
+    }
     if (rc != DBM_OK) {
         delete h;
         return rc;
@@ -928,6 +933,7 @@ struct dbm_batch_s {
     KernelInfo ki;
     int variant;
     int grid;
+    int nsm;
     cudaGraphExec_t graph;    // GRAPH_STEPS batch steps + counter advance
 };
 
@@ -1093,6 +1099,7 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
         delete b;
         return cuda_fail(e, "dbm_batch_create");
     }
+    b->nsm = nsm;
     b->grid = nsm * std::max(1, b->ki.blocks_per_sm);
     b->dirty = true;
     *out = b;
@@ -1146,6 +1153,30 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
 {
     if (!b) return DBM_EINVAL;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // Kernel variant: the tensor-map default only if every attached instance
+    // has its maps encoded with this kernel's tile width.
+    {
+        int v = b->precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
+        KernelInfo ki;
+        CK(b->precision == DBM_FP64 ? batch_kernel_info<double>(v, &ki) : batch_kernel_info<float>(v, &ki));
+        bool maps_ok = true;
+        for (int s = 0; s < b->max_slots; ++s)
+            if (b->inst[s] && (!b->inst[s]->tmap_ok || b->inst[s]->ki.W != ki.W)) maps_ok = false;
+        if (ki.version == 3 && !maps_ok) {
+            v = b->precision == DBM_FP64 ? fallback_variant<double>() : fallback_variant<float>();
+            CK(b->precision == DBM_FP64 ? batch_kernel_info<double>(v, &ki) : batch_kernel_info<float>(v, &ki));
+        }
+        if (v != b->variant) {
+            if (b->graph) {  // captured with the other kernel
+                CK(cudaStreamSynchronize(st));
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+            b->variant = v;
+            b->ki = ki;
+            b->grid = b->nsm * std::max(1, ki.blocks_per_sm);
+        }
+    }
     // item table: W sites x rows_per_item rows of every attached instance
     long long n = 0;
     for (int s = 0; s < b->max_slots; ++s) {
@@ -1241,9 +1272,11 @@ int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream)
     return DBM_OK;
 }
 
-int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item)
+int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item,
+                          int *variant)
 {
     if (!b) return DBM_EINVAL;
+    if (variant) *variant = b->variant;
     if (grid) *grid = b->grid;
     if (items) *items = b->n_items;
     if (rows_per_item) *rows_per_item = b->rows_per_item;

@@ -95,6 +95,14 @@ __device__ __forceinline__ void fence_proxy_async_smem()
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// A tensor map read from global memory (the batch slot table, written by host
+// copies) must be made visible to the tensor-map proxy before the first
+// tensor copy that uses it.
+__device__ __forceinline__ void fence_tensormap_acquire(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(map) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
@@ -724,6 +732,10 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 // (lambda), one bulk copy (trig row); the box starts at the
                 // halo column pj0 - HALO and out-of-range columns are zeros
                 if (lane == 0) {
+                    if (Work::kCopyArgs && p_row == 0) {  // maps of a batch slot, in global memory
+                        fence_tensormap_acquire(&pa->tm_f);
+                        fence_tensormap_acquire(&pa->tm_lam);
+                    }
                     mbar_arrive_expect_tx(&full[slot], (uint32_t)(WP * NARR + TAB) * (uint32_t)sizeof(real));  // 33 + 1 rows + trig
                     fence_proxy_async_smem();
                     tma_load_3d(buf, &pa->tm_f, pj0 - HALO, m, 0, &full[slot]);

@@ -8,7 +8,8 @@
 #define DBM_REAL float
 #define DBM_VARIANTS(X) X(1, 1, 128, 6, false, 2) X(2, 2, 128, 6, false, 2) X(3, 2, 128, 4, true, 3) \
     X(4, 3, 128, 6, false, 2) X(5, 3, 128, 4, true, 3)
-#define DBM_DEFAULT_VARIANT 2
+#define DBM_DEFAULT_VARIANT 4
+#define DBM_FALLBACK_VARIANT 2
 #include "dbm_launch_impl.cuh"
 
 namespace dbm {

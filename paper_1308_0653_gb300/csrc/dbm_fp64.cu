@@ -8,4 +8,5 @@
 #define DBM_VARIANTS(X) X(1, 1, 64, 5, false, 2) X(2, 2, 64, 5, false, 2) X(3, 2, 64, 4, true, 3) \
     X(4, 3, 64, 5, false, 2) X(5, 3, 64, 4, true, 3)
 #define DBM_DEFAULT_VARIANT 2
+#define DBM_FALLBACK_VARIANT 2
 #include "dbm_launch_impl.cuh"

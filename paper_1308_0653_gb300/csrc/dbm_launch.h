@@ -15,7 +15,8 @@ struct KernelInfo {
     int halo;          // halo columns per side (16 bytes)
     int smem;          // dynamic shared memory per CTA (bytes)
     int blocks_per_sm; // resident CTAs per SM
-    int version;       // 1: CTA-wide row barrier, 2: producer warp + full/empty barriers
+    int version;       // 1: CTA-wide row barrier, 2: producer warp + full/empty barriers,
+                       // 3: as 2 with rows loaded by tensor-map TMA
 };
 
 constexpr int MAX_VARIANTS = 8;
@@ -23,6 +24,8 @@ constexpr int MAX_VARIANTS = 8;
 // Kernel variants of one precision are numbered 1..num_variants<real>().
 template <typename real> int num_variants();
 template <typename real> int default_variant();
+// The default when tensor maps cannot be used (a variant with version < 3).
+template <typename real> int fallback_variant();
 template <typename real> cudaError_t kernel_info(int variant, KernelInfo *out);
 template <typename real> cudaError_t launch_step(int variant, const StepArgs<real> &A, int grid, cudaStream_t s);
 template <typename real> cudaError_t batch_kernel_info(int variant, KernelInfo *out);

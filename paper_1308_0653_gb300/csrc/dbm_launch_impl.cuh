@@ -1,6 +1,7 @@
 // Instantiates the kernels of one precision; included once per precision
 // translation unit with DBM_REAL and the variant list DBM_VARIANTS(X) defined,
-// X(id, version, W, NSTAGE, REREAD, MIN_BLOCKS_PER_SM), and DBM_DEFAULT_VARIANT.
+// X(id, version, W, NSTAGE, REREAD, MIN_BLOCKS_PER_SM), DBM_DEFAULT_VARIANT and
+// DBM_FALLBACK_VARIANT (the default when tensor maps are unavailable).
 // version 1: CTA-wide row barrier; 2: producer warp, per-array bulk copies;
 // 3: producer warp, tensor-map TMA tiles.
 #include "dbm_launch.h"
@@ -80,6 +81,7 @@ template <> int num_variants<DBM_REAL>()
 }
 
 template <> int default_variant<DBM_REAL>() { return DBM_DEFAULT_VARIANT; }
+template <> int fallback_variant<DBM_REAL>() { return DBM_FALLBACK_VARIANT; }
 
 template <>
 cudaError_t kernel_info<DBM_REAL>(int variant, KernelInfo *out)

@@ -103,7 +103,7 @@ def lib():
         L.dbm_batch_time.restype = ctypes.c_int64
         L.dbm_batch_commit.argtypes = [B, vp]
         L.dbm_batch_step.argtypes = [B, ctypes.c_int64, vp]
-        L.dbm_batch_launch_info.argtypes = [B] + [ctypes.POINTER(ctypes.c_int)] * 3
+        L.dbm_batch_launch_info.argtypes = [B] + [ctypes.POINTER(ctypes.c_int)] * 4
         _lib = L
     return _lib
 
@@ -295,9 +295,9 @@ def dbm_batch_step(b, nsteps, stream=None):
 
 
 def dbm_batch_launch_info(b) -> dict:
-    vals = [ctypes.c_int(0) for _ in range(3)]
+    vals = [ctypes.c_int(0) for _ in range(4)]
     _check(lib().dbm_batch_launch_info(b, *[ctypes.byref(v) for v in vals]), "dbm_batch_launch_info")
-    return dict(zip(("grid", "items", "rows_per_item"), [v.value for v in vals]))
+    return dict(zip(("grid", "items", "rows_per_item", "variant"), [v.value for v in vals]))
 
 
 # ---- convenience ----------------------------------------------------------

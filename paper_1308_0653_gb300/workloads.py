@@ -142,16 +142,16 @@ def implosion(nr: int = 2048, ntheta: int = 2048, nsteps: int = 20000, seed: int
 
 
 def planar_cj(nr: int = 20000, ntheta: int = 8, dt: float = 2.5e-7, t_end: float = 0.025,
-              precision: str = "fp64") -> Workload:
+              precision: str = "fp64", sector: int = 0) -> Workload:
     """Steady planar detonation of the validation run (Sec. III.B): annulus
     r in [1000, 1000.1]; Chapman-Jouguet burnt state (1.35826, 2.59709, 0.81650,
     0, 1) for r <= 1000.01, unburnt (1, 1, 0, 0, 0) outside; tau 2e-4,
-    omega1 10, omega2 1000.  ntheta = 8 with axisymmetric data reproduces the
-    paper's one-cell pi/4 sector on a full 2 pi grid."""
+    omega1 10, omega2 1000.  ntheta = 8 with axisymmetric data on a full 2 pi
+    grid reproduces the paper's one-cell pi/4 sector (sector = 1, ntheta = 1)."""
     p = base_params(nr=nr, ntheta=ntheta, r_in=1000.0, r_out=1000.1, dt=dt, tau=2e-4,
-                    omega1=10.0, omega2=1000.0, precision=precision)
+                    omega1=10.0, omega2=1000.0, precision=precision, sector=sector)
     f = _two_state(nr, ntheta, 1000.0, 1000.1, lambda r, th: r <= 1000.01,
-                   (1.35826, 0.81650, 0.0, 2.59709, 1.0), (1.0, 0.0, 0.0, 1.0, 0.0))
+                   (1.35826, 0.81650, 0.0, 2.59709, 1.0), (1.0, 0.0, 0.0, 1.0, 0.0), sector)
     return Workload(f"planar_cj{nr}", p, f, int(round(t_end / dt)))
 
 

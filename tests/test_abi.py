@@ -24,7 +24,7 @@ def declared_functions():
     return sorted(names)
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_step_path_entry_points():
     names = declared_functions()
     for n in ("dbm_create", "dbm_init_state", "dbm_step", "dbm_moments", "dbm_destroy"):
         assert n in names

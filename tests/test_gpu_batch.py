@@ -20,8 +20,8 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-def _alone(w, precision, nsteps):
-    sim = dbm.Simulation(dict(w.params, precision=precision))
+def _alone(w, precision, nsteps, variant=0):
+    sim = dbm.Simulation(dict(w.params, precision=precision, variant=variant))
     sim.init_state(w.fields)
     sim.step(nsteps)
     st = sim.export_state()
@@ -42,10 +42,15 @@ def test_batch_equals_alone_bitwise(precision):
         sims.append(s)
     b.step(90)
     assert b.time() == 90
+    # FP32 batches load rows through the slots' tensor maps; the reference
+    # runs alone with per-array bulk copies (variant 2), so the comparison
+    # also crosses the two ways of loading a row
+    info = b.launch_info()
+    assert info["variant"] == (4 if precision == "fp32" else 2)
     for s, w, n in zip(sims, ws, steps):
         assert dbm.dbm_steps_done(s.h) == n
         got = s.export_state()
-        ref = _alone(w, precision, n)
+        ref = _alone(w, precision, n, variant=2)
         assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), w.name
     b.close()
     for s in sims:
