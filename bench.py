@@ -43,7 +43,10 @@ FALLBACK_HBM_GBS = 6800.0
 # summary with its command is in profiles/).  A capture counts only while the
 # kernel and launch sources still hash to the value it was taken with.
 KERNEL_SOURCES = ("dbm_device.cuh", "dbm_launch.h", "dbm_launch_impl.cuh", "dbm_fp32.cu", "dbm_api.cu")
-TRAFFIC_CAPTURES = []  # dicts: variant, nr, ntheta, bytes, sources_sha256
+TRAFFIC_CAPTURES = [  # profiles/step_kernel_fp32_v4_implosion2048_dram.md
+    {"variant": 4, "nr": 2048, "ntheta": 2048, "bytes": 1105170000,
+     "sources_sha256": "85be285f2c9be1efa0b026d3fdf5bc33a34ef29f3a256c73434e54c665d68bf6"},
+]
 
 
 def kernel_sources_sha256():
@@ -82,6 +85,8 @@ def parse():
                     help="step: the default line; batch: 64 uneven instances in one persistent "
                          "launch per step; serve: Poisson arrivals through dbm_submit/dbm_poll")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--rows-per-item", type=int, default=0,
+                    help="theta rows per work item of batches and the server (0 = library default)")
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=60.0)
@@ -420,12 +425,12 @@ def run_batch(args):
         s = dbm.Simulation(dict(w.params, precision="fp32"))
         s.init_state(w.fields, stream=stream)
         sims.append(s)
-    items = sum(((w.params["nr"] + 127) // 128) * ((w.params["ntheta"] + 15) // 16) for w in ws)
-    b = dbm.Batch(len(ws), items + 16, precision="fp32", rows_per_item=16)
+    b = dbm.Batch(len(ws), 1 << 22, precision="fp32", rows_per_item=args.rows_per_item)
     for k, s in enumerate(sims):
         b.attach(k, s, args.batch_steps)
     b.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
+    info = b.launch_info()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps = args.batch_steps - args.warmup
     e0.record(stream)
@@ -454,7 +459,7 @@ def run_batch(args):
             "config": {"workload": f"{len(ws)} instances, N x N with N uniform in [128, 1024] "
                                    "(seed 0), explosion/implosion alternating, shock ratio "
                                    "logU[1.2, 3], omega1 logU[0.5, 8]",
-                       "sites": sites, "work_items": items},
+                       "sites": sites, "launch": info},
             "one_by_one": {"value": alone, "unit": UNIT,
                            "how": "each instance alone, 64 graph-replayed steps, summed time"},
             "batched_over_one_by_one": batched / alone}
@@ -471,7 +476,7 @@ def run_serve(args):
     free, total = torch.cuda.mem_get_info()
     pool = int(min(free * 0.8, 150e9))
     srv = dbm.Server(pool_bytes=pool, max_slots=64, max_queue=100000, quantum=64,
-                     max_items=1 << 20, rows_per_item=16)
+                     max_items=1 << 20, rows_per_item=args.rows_per_item)
     arr = W.arrivals(args.rate, args.duration, seed=0)
     t0 = time.perf_counter()
     tickets = []

@@ -56,7 +56,7 @@ def runs():
         finally:
             sim.close()
         f1, f = _front(r, m1["lam"][0]), _front(r, m["lam"][0])
-        out[prec] = dict(r=r, m={k: v[0] for k, v in m.items()}, front=f,
+        out[prec] = dict(r=r, m={k: m[k][0] for k in ("rho", "ur", "uth", "T", "lam")}, front=f,
                          D=(f - f1) / ((n - n1) * dt), dr=r[1] - r[0])
     return out
 
