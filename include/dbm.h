@@ -199,7 +199,9 @@ int dbm_status(dbm_t *h, void *stream);
 /* Checkpoint: copy the raw state to host memory.  f receives 33 * ntheta * nr
  * values and lam ntheta * nr values in the handle's precision (float for
  * DBM_FP32, double for DBM_FP64), layout f[v][ntheta][nr]; *steps receives the
- * step counter.  Synchronises `stream`. */
+ * step counter.  lam holds the stored reaction variable: lambda for DBM_FP64,
+ * the unburnt fraction 1 - lambda for DBM_FP32 (floats near 1 are too coarse
+ * for the last stages of burning).  Synchronises `stream`. */
 int dbm_export_state(dbm_t *h, void *f, void *lam, int64_t *steps, void *stream);
 
 /* Restore a state written by dbm_export_state (same layout and precision);

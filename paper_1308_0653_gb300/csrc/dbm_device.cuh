@@ -4,7 +4,8 @@
 // Data layout in HBM (one instance):
 //   f[v][theta][ld]   33 planes, row length ld = nr rounded up to 32 elements,
 //                     r contiguous (coalesced 128-byte rows)
-//   lam[theta][ld]    reaction progress lambda
+//   lam[theta][ld]    reaction variable: lambda (FP64) or 1 - lambda (FP32,
+//                     see LamStore)
 //   rowtab[theta][16] cos(i pi/4 - theta_m), sin(i pi/4 - theta_m), i = 0..7
 //   inv_r[ld]         1 / r_j at cell centres
 //
@@ -220,6 +221,26 @@ template <> struct Op<double> {
 };
 
 // ---------------------------------------------------------------------------
+// Stored reaction variable.  FP64 stores lambda itself.  FP32 stores the
+// unburnt fraction y = 1 - lambda: as lambda -> 1 the reaction increments per
+// step fall below half the spacing of floats just under 1 (6e-8) and would
+// round away, so lambda would stall short of 1 while the heat release
+// computed from (1 - lambda) went on; y keeps them with full relative
+// precision.  Near lambda = 0 the spacing of y (6e-8) bounds the absolute
+// error of a step instead, far below the reaction increments there.
+// ---------------------------------------------------------------------------
+template <typename real> struct LamStore {
+    static constexpr bool complement = false;
+    static __host__ __device__ __forceinline__ double to_lambda(double s) { return s; }
+    static __host__ __device__ __forceinline__ double from_lambda(double l) { return l; }
+};
+template <> struct LamStore<float> {
+    static constexpr bool complement = true;
+    static __host__ __device__ __forceinline__ double to_lambda(double s) { return 1.0 - s; }
+    static __host__ __device__ __forceinline__ double from_lambda(double l) { return 1.0 - l; }
+};
+
+// ---------------------------------------------------------------------------
 // One site's update (Eq. LB_evolution_equation, Eq. Eqlambda), all 33
 // velocities unrolled.  sp/sc/sn: shared-memory buffers of rows m-1, m, m+1;
 // col = HALO + tx.  Velocity (k, i) has Cartesian direction i pi / 4, so its
@@ -240,7 +261,9 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     real f[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) f[q] = sc[q * WP + col];
-    const real lam = sc[LAMOFF + col];
+    constexpr bool kY = LamStore<real>::complement;
+    const real lst = sc[LAMOFF + col];  // stored: lambda, or y = 1 - lambda
+    const real lam = kY ? O::sub(one, lst) : lst;
 
     // --- a2: moments, ring by ring (Cartesian components) ------------------
     //     rho = sum f, rho u = sum f v, e2 = sum f v^2, T = (e2/rho - u^2)/2
@@ -303,7 +326,7 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
             b = O::mul(A.omega2, P);
         }
     }
-    const real om = O::sub(one, lam);
+    const real om = kY ? lst : O::sub(one, lam);  // 1 - lambda
     const real g = O::fma(b, lam, a);  // a + b lam
     real R = O::mul(om, g);
     const real sab = O::add(a, b);
@@ -381,11 +404,13 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     const real uth = O::fma(uy, cth, -O::mul(ux, sth));
     int orr = ur >= real(0) ? -1 : 1;
     if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
+    // transport acts on the stored variable alike (y - y_nb = lambda_nb - lambda);
+    // the reaction step adds dlam to lambda, so it is taken off y
     const real lr = sc[LAMOFF + col + orr];
     const real lt = (uth >= real(0) ? sp : sn)[LAMOFF + col];
-    real ln = O::add(lam, dlam);
-    ln = O::sub(ln, O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lam, lr)));
-    ln = O::sub(ln, O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lam, lt)));
+    real ln = kY ? O::sub(lst, dlam) : O::add(lst, dlam);
+    ln = O::sub(ln, O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lst, lr)));
+    ln = O::sub(ln, O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lst, lt)));
     ln = fmin(fmax(ln, real(0)), real(1));
     A.lam_out[(long long)m * A.ld + j] = ln;
 }
@@ -931,7 +956,7 @@ __global__ void init_kernel(const InitArgs<real> A)
                 out[(long long)(1 + 8 * k + i) * A.plane] = (real)(rho * F[k] * poly);
             }
         }
-        A.lam[(long long)m * A.ld + j] = (real)lam;
+        A.lam[(long long)m * A.ld + j] = (real)LamStore<real>::from_lambda(lam);
     }
 }
 
@@ -987,7 +1012,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
         double sth, cth;
         sincospi(A.th_over_pi * m, &sth, &cth);
         const double ur = ux * cth + uy * sth, uth = -ux * sth + uy * cth;
-        const double lam = (double)A.lam[(long long)m * A.ld + j];
+        const double lam = LamStore<real>::to_lambda((double)A.lam[(long long)m * A.ld + j]);
         if (A.out) {
             A.out[s] = rho;
             A.out[N + s] = ur;

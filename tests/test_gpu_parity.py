@@ -181,3 +181,18 @@ def test_autotune_picks_a_variant_and_keeps_the_update(orc):
     sim2 = dbm.Simulation(dict(w.params, precision="fp32"))
     assert sim2.launch_info()["variant"] == best
     sim2.close()
+
+
+def test_fp32_burning_completes_as_lambda_approaches_one(orc):
+    """A hot gas at rest that is almost burnt (lambda = 1 - 1e-5) keeps
+    burning in FP32 as in the FP64 oracle: 1 - lambda decays by e^-4 over
+    1000 steps.  Per-step increments of lambda here (4e-8 down to 7e-10)
+    are below the spacing of floats just under 1, so a lambda stored as a
+    float would stall; the FP32 path stores 1 - lambda and tracks the oracle
+    to 1e-3 relative in 1 - lambda itself."""
+    w = W.uniform_state(32, 8, 1.0, 0.0, 0.0, 2.0, 1.0 - 1e-5, dt=1e-5, omega1=100.0, omega2=100.0)
+    out = run_gpu(w, "fp32", nsteps=1000)
+    ref = run_oracle(orc, w, nsteps=1000)
+    y_gpu, y_ref = 1.0 - out["lam"], 1.0 - ref["lam"]
+    assert y_ref.max() < 2.5e-7  # the oracle did burn
+    np.testing.assert_allclose(y_gpu, y_ref, rtol=1e-3)
