@@ -796,24 +796,8 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         int base = 0;
         int parity = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
-            const StepArgs<real> *ga;
-            int j0, mb, me;
-            if (!work.item(it, ga, j0, mb, me)) continue;
-            const StepArgs<real> *ap = ga;
-            if constexpr (Work::kCopyArgs) {
-                // per-instance constants into shared memory, double-buffered:
-                // the barrier of the previous item guarantees nobody still
-                // reads the copy made two items ago
-                StepArgs<real> *dst = sargs2 + parity;
-                const int nw = (int)(sizeof(StepArgs<real>) / sizeof(int));
-                for (int q = tx; q < nw; q += W)
-                    reinterpret_cast<int *>(dst)[q] = reinterpret_cast<const int *>(ga)[q];
-                named_bar_sync(1, W);
-                ap = dst;
-                parity ^= 1;
-            }
-            const StepArgs<real> &A = *ap;
+        // One work item: rows [mb, me) of the strip starting at radial site j0.
+        auto run_item = [&](const StepArgs<real> &A, int j0, int mb, int me) {
             const int L = me - mb;
             const int j = j0 + tx;
             const bool active = j < A.nr;
@@ -828,7 +812,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 }
                 if (*(volatile int *)&abort_flag) {
                     ok = false;
-                    break;
+                    return;
                 }
                 const real *sc = sm + (P % NSTAGE) * SLOT;
                 if (active) {
@@ -853,6 +837,29 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 }
             }
             base += L + 2;
+        };
+        for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+            const StepArgs<real> *ga;
+            int j0, mb, me;
+            if (!work.item(it, ga, j0, mb, me)) continue;
+            if constexpr (Work::kCopyArgs) {
+                // per-instance constants into shared memory, double-buffered:
+                // the barrier of the previous item guarantees nobody still
+                // reads the copy made two items ago
+                StepArgs<real> *dst = sargs2 + parity;
+                const int nw = (int)(sizeof(StepArgs<real>) / sizeof(int));
+                for (int q = tx; q < nw; q += W)
+                    reinterpret_cast<int *>(dst)[q] = reinterpret_cast<const int *>(ga)[q];
+                named_bar_sync(1, W);
+                parity ^= 1;
+                // and from there into registers for the item: the update reads
+                // about 40 of them per site, which a single instance takes from
+                // the constant bank as instruction operands
+                const StepArgs<real> Areg = *dst;
+                run_item(Areg, j0, mb, me);
+            } else {
+                run_item(*ga, j0, mb, me);
+            }
         }
     }
     __syncthreads();
