@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--smax", type=int, default=20000)
+    ap.add_argument("--batch-nmin", type=int, default=128, help="smallest side of a batch instance")
+    ap.add_argument("--batch-nmax", type=int, default=1024, help="largest side of a batch instance")
     ap.add_argument("--nmax", type=int, default=2048)
     return ap.parse_args()
 
@@ -411,13 +413,32 @@ def run_ours(args):
 GRAPH_WARM = 64
 
 
+def single_instance_glups(stream, steps=500):
+    """FP32 GLUPS of one 2048^2 implosion alone (the default step-mode workload),
+    for the batched and served ratios."""
+    import torch
+    from paper_1308_0653_gb300 import dbm
+    w1 = W.implosion(2048, 2048, nsteps=0)
+    s1 = dbm.Simulation(dict(w1.params, precision="fp32"))
+    s1.init_state(w1.fields, stream=stream)
+    s1.step(64, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s1.step(steps, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s1.close()
+    return w1.sites * NV * steps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
 def run_batch(args):
     """64 uneven square instances (N in [128, 1024], seeded) advanced together,
     one persistent launch per step, against the same instances run one by one."""
     import torch
     from paper_1308_0653_gb300 import dbm
     torch.cuda.set_device(0)
-    ws = W.batch(args.instances, seed=0, nsteps=args.batch_steps, align=1)
+    ws = W.batch(args.instances, seed=0, nsteps=args.batch_steps, nmin=args.batch_nmin,
+                 nmax=args.batch_nmax, align=1)
     sites = sum(w.sites for w in ws)
     stream = torch.cuda.Stream()
     sims = []
@@ -453,16 +474,21 @@ def run_batch(args):
     alone = sites * NV / t_one / 1e9
     for s in sims:
         s.close()
+    single = single_instance_glups(stream)
     line = {"metric": METRIC + ", batched sweep", "value": batched, "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(ws)} instances, N x N with N uniform in [128, 1024] "
+            "config": {"workload": f"{len(ws)} instances, N x N with N uniform in "
+                                   f"[{args.batch_nmin}, {args.batch_nmax}] "
                                    "(seed 0), explosion/implosion alternating, shock ratio "
                                    "logU[1.2, 3], omega1 logU[0.5, 8]",
                        "sites": sites, "launch": info},
             "one_by_one": {"value": alone, "unit": UNIT,
                            "how": "each instance alone, 64 graph-replayed steps, summed time"},
-            "batched_over_one_by_one": batched / alone}
+            "batched_over_one_by_one": batched / alone,
+            "single_instance": {"value": single, "unit": UNIT,
+                                "workload": "reactive implosion 2048x2048, 500 steps"},
+            "batched_over_single_instance": batched / single}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -496,6 +522,7 @@ def run_serve(args):
     stats = srv.stats()
     srv.close()
     executed_glups = stats["executed"] / wall / 1e9
+    single = single_instance_glups(torch.cuda.Stream())
     lat = np.array(lat) if lat else np.array([np.nan])
     line = {"metric": METRIC + ", served", "value": upd / wall / 1e9, "unit": UNIT, "n_gpus": 1,
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -506,6 +533,9 @@ def run_serve(args):
             "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.nanpercentile(lat, 50)),
             "p99_s": float(np.nanpercentile(lat, 99)), "backlog": len(tickets) - int(np.isfinite(lat).sum()),
             "executed_glups": executed_glups,
+            "single_instance": {"value": single, "unit": UNIT,
+                                "workload": "reactive implosion 2048x2048, 500 steps"},
+            "executed_over_single_instance": executed_glups / single,
             "offered_glups": sum(w.sites * NV * w.nsteps for _, w in tickets) / args.duration / 1e9,
             "server": stats}
     print(json.dumps(line), flush=True)

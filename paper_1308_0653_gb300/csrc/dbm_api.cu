@@ -13,6 +13,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <type_traits>
 #include <vector>
 
@@ -983,6 +984,50 @@ void fill_slot(dbm_batch_t *b, int s, unsigned char *dst)
     std::memcpy(dst, &sl, sizeof(sl));
 }
 
+// Static load balance of the batch's work items over the persistent CTAs.
+// CTA c runs items c, c + grid, c + 2 grid, ...  Items differ in cost: a strip
+// that overhangs its instance's last radial site has idle lanes, and the
+// ragged last run of rows is short.  Longest-processing-time-first: items in
+// decreasing estimated cost (ties keep the interleaved order), each to the
+// least loaded CTA; then laid out so CTA c finds its k-th item at k grid + c,
+// padding with empty items (slot -1).  Cost estimate of an item of L rows and
+// a active lanes of W: (L + 2) (0.3 + 0.7 a / W): every row moves through the
+// CTA's pipeline, and the update time grows with the active lanes.  Returns
+// the new item count; keeps the interleaved order if the padded table would
+// exceed max_items.
+long long balance_items(int4 *items, long long n, int grid, int W, const std::vector<dbm_t *> &inst,
+                        long long max_items)
+{
+    if (n <= grid || grid < 1) return n;
+    std::vector<double> cost(n);
+    for (long long i = 0; i < n; ++i) {
+        const int4 e = items[i];
+        const int active = std::min(W, inst[e.x]->p.nr - e.y);
+        cost[i] = (double)(e.w - e.z + 2) * (0.3 + 0.7 * (double)active / W);
+    }
+    std::vector<long long> order(n);
+    for (long long i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](long long a, long long c) { return cost[a] > cost[c]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+    std::vector<std::vector<int4>> bins(grid);
+    for (long long i : order) {
+        Load l = heap.top();
+        heap.pop();
+        bins[l.second].push_back(items[i]);
+        heap.push({l.first + cost[i], l.second});
+    }
+    size_t K = 0;
+    for (const auto &bin : bins) K = std::max(K, bin.size());
+    const long long total = (long long)K * grid;
+    if (total > max_items) return n;
+    for (size_t k = 0; k < K; ++k)
+        for (int c = 0; c < grid; ++c)
+            items[k * grid + c] = k < bins[c].size() ? bins[c][k] : make_int4(-1, 0, 0, 0);
+    return total;
+}
+
 int batch_launch(dbm_batch_t *b, int s, cudaStream_t st)
 {
     cudaError_t e;
@@ -1222,6 +1267,7 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
             more = true;
         }
     }
+    n = balance_items(items, n, b->grid, b->ki.W, b->inst, b->max_items);
     b->n_items = (int)n;
     std::memcpy(b->stage + b->off_nitems, &b->n_items, sizeof(int));
     CK(cudaMemcpyAsync(b->buf + b->off_slots, b->stage, (size_t)b->max_slots * b->slot_bytes,

@@ -471,6 +471,7 @@ struct BatchWork {
                                          int &me) const
     {
         const int4 e = items[it];
+        if (e.x < 0) return false;  // padding of the load-balanced table
         const BatchSlot<real> &sl = slots[e.x];
         if (T < sl.start || T >= sl.end) return false;
         a = &sl.args[(int)((T - sl.start + sl.par0) & 1)];
