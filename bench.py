@@ -447,8 +447,16 @@ def run_batch(args):
         s.init_state(w.fields, stream=stream)
         sims.append(s)
     b = dbm.Batch(len(ws), 1 << 22, precision="fp32", rows_per_item=args.rows_per_item)
+    tune_steps = 64
     for k, s in enumerate(sims):
-        b.attach(k, s, args.batch_steps)
+        b.attach(k, s, args.batch_steps + 6 * (32 + tune_steps))
+    tune = None
+    if args.rows_per_item == 0:
+        # batch autotuner on the live batch: kernel x rows per item
+        v, r, ms = b.autotune(steps=tune_steps, stream=stream)
+        names = [f"v{vv}/r{rr}" for vv in (4, 2) for rr in (16, 32, 64)]
+        tune = {"variant": v, "rows_per_item": r,
+                "ms_per_step": {n: round(x, 4) for n, x in zip(names, ms) if x > 0}}
     b.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     info = b.launch_info()
@@ -482,7 +490,7 @@ def run_batch(args):
                                    f"[{args.batch_nmin}, {args.batch_nmax}] "
                                    "(seed 0), explosion/implosion alternating, shock ratio "
                                    "logU[1.2, 3], omega1 logU[0.5, 8]",
-                       "sites": sites, "launch": info},
+                       "sites": sites, "launch": info, "autotune": tune},
             "one_by_one": {"value": alone, "unit": UNIT,
                            "how": "each instance alone, 64 graph-replayed steps, summed time"},
             "batched_over_one_by_one": batched / alone,

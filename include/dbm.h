@@ -129,8 +129,10 @@ size_t dbm_state_bytes(const dbm_params *p);
 
 /* Bind a simulation to caller device memory dev_buf (dev_bytes >=
  * dbm_state_bytes(p), 256-byte aligned, on the current device).  Uploads the
- * geometry tables and clears the buffer (synchronous).  The caller keeps
- * ownership of dev_buf and must keep it alive until dbm_destroy.
+ * geometry tables and clears the buffer on the legacy default stream and
+ * waits for that stream only (work in flight on non-blocking streams goes on;
+ * none of it may touch dev_buf).  The caller keeps ownership of dev_buf and
+ * must keep it alive until dbm_destroy.
  * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (buffer too small), DBM_ECUDA. */
 int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out);
 
@@ -324,6 +326,18 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream);
  * attached simulation advances while it has steps left. */
 int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
 
+/* Autotuner of a batch: times the precision's default kernel and the
+ * bulk-copy kernel, each with 16, 32 and 64 theta rows per work item, for
+ * `steps` batched steps each (after 32 untimed steps) with CUDA
+ * events on `stream`, and keeps the fastest.  The trials advance every
+ * attached simulation (6 x (32 + steps) steps at most); attach them with
+ * enough steps left.  *variant and *rows_per_item receive the choice;
+ * ms_per_step[6] (may be NULL) the time per step of each candidate in the
+ * order (default, 16), (default, 32), (default, 64), (bulk, 16), (bulk, 32),
+ * (bulk, 64); 0 for a candidate not run.  Errors: DBM_EINVAL, DBM_ECUDA. */
+int dbm_batch_autotune(dbm_batch_t *b, int steps, void *stream, int *variant, int *rows_per_item,
+                       float *ms_per_step);
+
 /* Launch shape: persistent grid, current number of work items, rows per item,
  * kernel variant (as of the last commit).  Null outputs are skipped. */
 int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows_per_item,
@@ -337,9 +351,13 @@ int dbm_batch_launch_info(const dbm_batch_t *b, int *grid, int *items, int *rows
  * (first fit in arrival order; a request passed over max_bypass times blocks
  * later ones until it starts), advances all resident simulations quantum by
  * quantum in shared launches, and retires finished ones: their moments go to
- * host memory and dbm_poll hands them out.  Per-request upload and download
- * run on a second stream and overlap the batched steps.  Each result equals
- * the result of running the request alone (same kernel, same bits).
+ * host memory and dbm_poll hands them out.  A quantum is `quantum` steps or
+ * fewer: it ends when the first resident simulation finishes, so the work
+ * items are rebalanced over the GPU for the simulations still running.  Two
+ * quanta are kept in flight, so admission, table updates and retirement on
+ * the host overlap the GPU.  Per-request upload and download run on a second
+ * stream and overlap the batched steps.  Each result equals the result of
+ * running the request alone (same kernel, same bits).
  */
 typedef struct dbm_server_s dbm_server_t;
 

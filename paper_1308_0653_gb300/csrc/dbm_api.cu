@@ -527,8 +527,11 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
         delete h;
         return rc;
     }
+    // cleared on the legacy stream, which the library's and the server's
+    // non-blocking streams do not wait for: no device-wide synchronisation
+    // (a server admits new simulations while a batched quantum runs)
     e = cudaMemset(dev_buf, 0, L.total);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) {
         delete h;
         return cuda_fail(e, "dbm_create: clear buffer");
@@ -933,6 +936,7 @@ struct dbm_batch_s {
     bool dirty;
     KernelInfo ki;
     int variant;
+    int forced_variant;       // 0: the precision's default (set by dbm_batch_autotune)
     int grid;
     int nsm;
     cudaGraphExec_t graph;    // GRAPH_STEPS batch steps + counter advance
@@ -1201,7 +1205,8 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
     // Kernel variant: the tensor-map default only if every attached instance
     // has its maps encoded with this kernel's tile width.
     {
-        int v = b->precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
+        int v = b->forced_variant > 0 ? b->forced_variant
+                : (b->precision == DBM_FP64 ? default_variant<double>() : default_variant<float>());
         KernelInfo ki;
         CK(b->precision == DBM_FP64 ? batch_kernel_info<double>(v, &ki) : batch_kernel_info<float>(v, &ki));
         bool maps_ok = true;
@@ -1315,6 +1320,63 @@ int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream)
         }
     }
     for (int s = 0; s < b->max_slots; ++s) batch_account(b, s, t0, b->T);
+    return DBM_OK;
+}
+
+int dbm_batch_autotune(dbm_batch_t *b, int steps, void *stream, int *variant, int *rows_per_item,
+                       float *ms_per_step)
+{
+    if (!b || steps < 1) return DBM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int vdef = b->precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
+    const int vfb = b->precision == DBM_FP64 ? fallback_variant<double>() : fallback_variant<float>();
+    const int vs[2] = {vdef, vfb};
+    const int rows[3] = {16, 32, 64};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int rc = DBM_OK, bestv = 0, bestr = 0;
+    float bestms = 0.f;
+    for (int c = 0; c < 6 && rc == DBM_OK; ++c) {
+        const int v = vs[c / 3], r = rows[c % 3];
+        if (ms_per_step) ms_per_step[c] = 0.f;
+        if (c >= 3 && vfb == vdef) continue;
+        b->forced_variant = v;
+        b->rows_per_item = r;
+        b->dirty = true;
+        rc = dbm_batch_step(b, GRAPH_STEPS, stream);  // commit, graph capture, warm-up
+        if (rc != DBM_OK) break;
+        if (b->variant != v) continue;  // the tensor-map kernel is not usable for this batch
+        cudaEventRecord(e0, st);
+        rc = dbm_batch_step(b, steps, stream);
+        cudaEventRecord(e1, st);
+        if (rc != DBM_OK) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "batch autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= steps;
+        if (ms_per_step) ms_per_step[c] = ms;
+        if (bestv == 0 || ms < bestms) {
+            bestv = v;
+            bestr = r;
+            bestms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DBM_OK) return rc;
+    if (bestv == 0) return DBM_ECUDA;
+    b->forced_variant = bestv;
+    b->rows_per_item = bestr;
+    b->dirty = true;
+    rc = dbm_batch_commit(b, stream);
+    if (rc != DBM_OK) return rc;
+    if (variant) *variant = bestv;
+    if (rows_per_item) *rows_per_item = bestr;
     return DBM_OK;
 }
 

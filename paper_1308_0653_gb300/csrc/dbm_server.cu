@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
@@ -102,6 +103,8 @@ struct Request {
     int slot = -1;
     size_t off = 0, bytes = 0;
     dbm_t *h = nullptr;
+    int64_t end_step = 0;        // batch step at which its last step is done
+    bool leaving = false;        // detached, waiting to be retired
     dbm_result res;
     int bypassed = 0;            // times a later request was admitted ahead of it
 };
@@ -198,7 +201,10 @@ void admit(dbm_server_t *S, Request *r, int slot, size_t off, size_t bytes)
         const double *f = r->init.data();
         rc = dbm_init_state(r->h, f, f + N, f + 2 * N, f + 3 * N, f + 4 * N, S->io);
     }
-    if (rc == DBM_OK) rc = dbm_batch_attach(S->batch, slot, r->h, r->nsteps);
+    if (rc == DBM_OK) {
+        r->end_step = dbm_batch_time(S->batch) + r->nsteps;
+        rc = dbm_batch_attach(S->batch, slot, r->h, r->nsteps);
+    }
     if (rc != DBM_OK) {
         if (r->h) dbm_destroy(r->h);
         r->h = nullptr;
@@ -212,15 +218,41 @@ void admit(dbm_server_t *S, Request *r, int slot, size_t off, size_t bytes)
     std::vector<double>().swap(r->init);  // the copy is on the device now
 }
 
+// The scheduler keeps up to two quanta in flight on the compute stream: it
+// enqueues quantum n, then waits for quantum n-1 while n runs, so the host
+// work between quanta (admission, table updates, retirement) overlaps the
+// GPU.  Which attached simulations advance in a step is decided on the device
+// from the batch step counter, so a simulation that ends inside a quantum
+// needs no table change to stop; it is detached once found finished and
+// retired (moments, destroy, free) as soon as no launch in flight can touch
+// its buffers: at once if it ended before the running quantum starts, else
+// once that quantum is done.  A cancelled simulation is active in the running
+// quantum and waits for it the same way.
 void scheduler(dbm_server_t *S)
 {
     cudaSetDevice(S->device);
-    cudaEvent_t quantum_done, io_done;
-    cudaEventCreateWithFlags(&quantum_done, cudaEventDisableTiming);
+    cudaEvent_t qdone[2], io_done;
+    cudaEventCreateWithFlags(&qdone[0], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&qdone[1], cudaEventDisableTiming);
     cudaEventCreateWithFlags(&io_done, cudaEventDisableTiming);
-    bool quantum_pending = false;
+    bool pend[2] = {false, false};
+    int64_t pend_seq[2] = {0, 0}, pend_start[2] = {0, 0};
+    int64_t qseq = 0;      // quanta enqueued so far
+    int64_t done_q = -1;   // every quantum up to this one is complete
+    struct Deferred {
+        Request *r;
+        bool cancelled;
+        int64_t wait_q;    // retire once this quantum is complete
+    };
+    std::vector<Deferred> deferred;
+    auto wait_slot = [&](int k) {
+        if (!pend[k]) return;
+        cudaEventSynchronize(qdone[k]);
+        pend[k] = false;
+        done_q = std::max(done_q, pend_seq[k]);
+    };
     for (;;) {
-        // ---- 1. admission (overlaps the quantum in flight) --------------------
+        // ---- 1. admission (overlaps the quanta in flight) ---------------------
         std::vector<std::pair<Request *, int>> to_admit;
         std::vector<std::pair<size_t, size_t>> blocks;
         {
@@ -229,8 +261,10 @@ void scheduler(dbm_server_t *S)
                 const bool any_running = S->stats.running > 0;
                 if (S->stop && S->queue.empty() && !any_running) {
                     lock.unlock();
-                    if (quantum_pending) cudaEventSynchronize(quantum_done);
-                    cudaEventDestroy(quantum_done);
+                    wait_slot(0);
+                    wait_slot(1);
+                    cudaEventDestroy(qdone[0]);
+                    cudaEventDestroy(qdone[1]);
                     cudaEventDestroy(io_done);
                     return;
                 }
@@ -283,53 +317,92 @@ void scheduler(dbm_server_t *S)
             cudaStreamWaitEvent(S->compute, io_done, 0);
         }
 
-        // ---- 2. the previous quantum is done: collect finished and cancelled --
-        if (quantum_pending) {
-            cudaEventSynchronize(quantum_done);
-            quantum_pending = false;
-        }
-        std::vector<std::pair<Request *, bool>> leaving;
+        // ---- 2. enqueue quantum n if anything is active ------------------------
+        // A quantum ends no later than the first active simulation does: the
+        // work items are balanced over the CTAs for the active set, and one
+        // that finishes early would leave its CTAs idle for the rest.
+        const int64_t t_now = dbm_batch_time(S->batch);
         bool any_active = false;
+        int64_t steps = S->cfg.quantum;
         {
             std::lock_guard<std::mutex> lock(S->mu);
             for (int k = 0; k < S->cfg.max_slots; ++k) {
                 Request *r = S->slots[k];
-                if (!r || !r->h || r->state != RUNNING) continue;
-                if (r->cancel || dbm_batch_remaining(S->batch, k) == 0) {
-                    leaving.push_back({r, r->cancel});
-                    dbm_batch_detach(S->batch, k);  // out of the next quantum's tables
-                } else {
+                if (!r || !r->h || r->state != RUNNING || r->leaving || r->cancel) continue;
+                const int64_t left = dbm_batch_remaining(S->batch, k);
+                if (left > 0) {
                     any_active = true;
+                    steps = std::min(steps, left);
                 }
             }
         }
-
-        // ---- 3. enqueue the next quantum --------------------------------------
+        double work = 0.0;  // site-velocity updates this quantum will execute
         if (any_active) {
-            double work = 0.0;  // site-velocity updates this quantum will execute
+            std::lock_guard<std::mutex> lock(S->mu);
             for (int k = 0; k < S->cfg.max_slots; ++k) {
                 Request *r = S->slots[k];
-                if (!r || !r->h || r->state != RUNNING) continue;
-                const int64_t left = dbm_batch_remaining(S->batch, k);
-                if (left > 0)
-                    work += (double)r->p.nr * r->p.ntheta * DBM_NV * (double)std::min<int64_t>(left, S->cfg.quantum);
+                if (!r || !r->h || r->state != RUNNING || r->leaving || r->cancel) continue;
+                if (dbm_batch_remaining(S->batch, k) > 0)
+                    work += (double)r->p.nr * r->p.ntheta * DBM_NV * (double)steps;
             }
-            {
-                std::lock_guard<std::mutex> lock(S->mu);
-                S->stats.executed += work;
-            }
-            const int rc = dbm_batch_step(S->batch, S->cfg.quantum, S->compute);
+        }
+        bool enqueued = false;
+        if (any_active) {
+            const int k = (int)(qseq & 1);
+            wait_slot(k);  // quantum n-2: at most two in flight
+            const int rc = dbm_batch_step(S->batch, steps, S->compute);
+            std::lock_guard<std::mutex> lock(S->mu);
             if (rc == DBM_OK) {
-                cudaEventRecord(quantum_done, S->compute);
-                quantum_pending = true;
+                cudaEventRecord(qdone[k], S->compute);
+                pend[k] = true;
+                pend_seq[k] = qseq;
+                pend_start[k] = t_now;
+                ++qseq;
+                enqueued = true;
+                S->stats.executed += work;
             } else {
-                std::lock_guard<std::mutex> lock(S->mu);
                 S->fatal = rc;
             }
         }
 
-        // ---- 4. retire while the quantum runs (their buffers are untouched) ---
-        for (auto &lr : leaving) retire(S, lr.first, lr.second);
+        // ---- 3. wait for quantum n-1 (or the last one, if none was enqueued) ---
+        for (int k = 0; k < 2; ++k)
+            if (pend[k] && (!enqueued || pend_seq[k] < qseq - 1)) wait_slot(k);
+        int64_t running_q = -1, running_from = INT64_MAX;  // the quantum still in flight
+        for (int k = 0; k < 2; ++k)
+            if (pend[k]) {
+                running_q = pend_seq[k];
+                running_from = pend_start[k];
+            }
+
+        // ---- 4. retire what no launch in flight touches ------------------------
+        std::vector<std::pair<Request *, bool>> now;
+        {
+            std::vector<Deferred> keep;
+            for (const Deferred &d : deferred) {
+                if (d.wait_q <= done_q)
+                    now.push_back({d.r, d.cancelled});
+                else
+                    keep.push_back(d);
+            }
+            deferred.swap(keep);
+        }
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            for (int k = 0; k < S->cfg.max_slots; ++k) {
+                Request *r = S->slots[k];
+                if (!r || !r->h || r->state != RUNNING || r->leaving) continue;
+                const bool finished = dbm_batch_remaining(S->batch, k) == 0;
+                if (!r->cancel && !finished) continue;
+                r->leaving = true;
+                dbm_batch_detach(S->batch, k);  // out of the next quantum's tables
+                if (running_q < 0 || (!r->cancel && r->end_step <= running_from))
+                    now.push_back({r, r->cancel});
+                else
+                    deferred.push_back({r, r->cancel, running_q});
+            }
+        }
+        for (auto &lr : now) retire(S, lr.first, lr.second);
     }
 }
 

@@ -104,6 +104,8 @@ def lib():
         L.dbm_batch_commit.argtypes = [B, vp]
         L.dbm_batch_step.argtypes = [B, ctypes.c_int64, vp]
         L.dbm_batch_launch_info.argtypes = [B] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.dbm_batch_autotune.argtypes = [B, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
         _lib = L
     return _lib
 
@@ -294,6 +296,15 @@ def dbm_batch_step(b, nsteps, stream=None):
     _check(lib().dbm_batch_step(b, int(nsteps), _stream(stream)), "dbm_batch_step")
 
 
+def dbm_batch_autotune(b, steps: int, stream=None):
+    """Returns (variant, rows_per_item, {(variant, rows): ms per step})."""
+    v, r = ctypes.c_int(0), ctypes.c_int(0)
+    ms = (ctypes.c_float * 6)()
+    _check(lib().dbm_batch_autotune(b, int(steps), _stream(stream), ctypes.byref(v), ctypes.byref(r), ms),
+           "dbm_batch_autotune")
+    return v.value, r.value, list(ms)
+
+
 def dbm_batch_launch_info(b) -> dict:
     vals = [ctypes.c_int(0) for _ in range(4)]
     _check(lib().dbm_batch_launch_info(b, *[ctypes.byref(v) for v in vals]), "dbm_batch_launch_info")
@@ -443,6 +454,9 @@ class Batch:
 
     def launch_info(self) -> dict:
         return dbm_batch_launch_info(self.b)
+
+    def autotune(self, steps: int = 64, stream=None):
+        return dbm_batch_autotune(self.b, steps, stream)
 
     def close(self):
         if self.b is not None:
