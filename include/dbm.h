@@ -221,6 +221,17 @@ int dbm_launch_info(const dbm_t *h, int *grid, int *threads, int *smem_bytes,
  * device floats d_x into d_approx and d_ieee (device arrays); asynchronous. */
 int dbm_selftest_rcp(const float *d_x, float *d_approx, float *d_ieee, int n, void *stream);
 
+/* Self-test of the bounded wait that every device-side wait of the step
+ * kernels uses (an mbarrier wait that gives up after a cycle limit, sets a
+ * status bit and returns instead of hanging).  One CTA waits on an mbarrier
+ * for at most limit_cycles (1 .. 2^31; the step kernels use 2^31, about a
+ * second): with arrive = 0 nothing arrives, the wait runs out and the kernel
+ * ORs 1 (the step kernels' "wait timed out" bit, reported by dbm_status as
+ * DBM_ETIMEOUT) into the device int *d_status; with arrive = 1 another warp
+ * arrives and *d_status is left unchanged.  Asynchronous on `stream`.
+ * Errors: DBM_EINVAL, DBM_ECUDA. */
+int dbm_selftest_wait(int *d_status, int arrive, int64_t limit_cycles, void *stream);
+
 /* Number of step-kernel variants for a precision (0 if invalid).  Variants
  * differ only in how the work is staged (pipeline, ring depth, registers);
  * every variant computes the same update bit for bit. */

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +22,14 @@
 #include "dbm_launch.h"
 
 using namespace dbm;
+
+namespace {
+// NVTX range for profilers (header-only NVTX3: no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -620,6 +629,7 @@ int dbm_init_state_device(dbm_t *h, const double *d_fields, void *stream)
 int dbm_step(dbm_t *h, int64_t nsteps, void *stream)
 {
     if (!h || nsteps < 0) return DBM_EINVAL;
+    NvtxRange range("dbm_step");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     while (nsteps > 0) {
         if (nsteps >= GRAPH_STEPS && h->cur == 0) {
@@ -838,6 +848,15 @@ int dbm_selftest_rcp(const float *d_x, float *d_approx, float *d_ieee, int n, vo
     if (!d_x || !d_approx || !d_ieee || n < 0) return DBM_EINVAL;
     cudaError_t e = launch_rcp_selftest(d_x, d_approx, d_ieee, n, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "rcp self-test launch");
+    return DBM_OK;
+}
+
+int dbm_selftest_wait(int *d_status, int arrive, int64_t limit_cycles, void *stream)
+{
+    if (!d_status || limit_cycles < 1 || limit_cycles > kWaitLimitCycles) return DBM_EINVAL;
+    cudaError_t e = launch_wait_selftest(d_status, arrive ? 1 : 0, (long long)limit_cycles,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test launch");
     return DBM_OK;
 }
 
@@ -1291,6 +1310,7 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
 int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream)
 {
     if (!b || nsteps < 0) return DBM_EINVAL;
+    NvtxRange range("dbm_batch_step");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (b->dirty) {
         int rc = dbm_batch_commit(b, stream);

@@ -125,12 +125,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Bounded wait: gives up after ~2^31 SM cycles (about a second) and reports false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+constexpr long long kWaitLimitCycles = 1LL << 31;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = kWaitLimitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -893,6 +896,23 @@ template <typename real, int W, int NSTAGE>
 constexpr int smem_bytes_v2()
 {
     return (int)(sizeof(real) * NSTAGE * V2Layout<real, W>::slot + 16 * NSTAGE);
+}
+
+// Self-test of the bounded wait every pipeline uses: one CTA waits on an
+// mbarrier with `limit` cycles.  With arrive = 0 nothing ever arrives, the
+// wait runs out and the kernel reports ST_WAIT_TIMEOUT in *status and returns
+// (the context stays usable); with arrive = 1 warp 1 arrives and the wait
+// succeeds.
+static __global__ void wait_selftest_kernel(int *status, int arrive, long long limit)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 32) mbar_arrive(&bar);
+    if (!mbar_wait_bounded(&bar, 0, limit) && (threadIdx.x & 31) == 0) atomicOr(status, ST_WAIT_TIMEOUT);
 }
 
 // Self-test of Op<float>::rcp against the correctly rounded division.

@@ -25,6 +25,12 @@ cudaError_t launch_rcp_selftest(const float *x, float *approx, float *ieee, int 
     return cudaGetLastError();
 }
 
+cudaError_t launch_wait_selftest(int *status, int arrive, long long limit, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 64, 0, s>>>(status, arrive, limit);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s)
 {
     batch_advance_kernel<<<1, 32, 0, s>>>(T, k);

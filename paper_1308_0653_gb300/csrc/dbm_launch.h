@@ -37,6 +37,7 @@ template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int 
 template <typename real> cudaError_t launch_noneq(const MomArgs<real> &A, int grid, cudaStream_t s);
 cudaError_t launch_totals(const double *partials, int nblocks, double *totals, cudaStream_t s);
 cudaError_t launch_rcp_selftest(const float *x, float *approx, float *ieee, int n, cudaStream_t s);
+cudaError_t launch_wait_selftest(int *status, int arrive, long long limit, cudaStream_t s);
 
 constexpr int MOMENT_BLOCKS = 1024;  // partial-sum slots of the totals reduction
 

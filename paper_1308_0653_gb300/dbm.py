@@ -85,6 +85,7 @@ def lib():
         L.dbm_launch_info.argtypes = [H] + [ctypes.POINTER(ctypes.c_int)] * 6
         L.dbm_noneq.argtypes = [H, _dp, vp]
         L.dbm_noneq_device.argtypes = [H, vp, vp]
+        L.dbm_selftest_wait.argtypes = [vp, ctypes.c_int, ctypes.c_int64, vp]
         L.dbm_num_variants.argtypes = [ctypes.c_int]
         L.dbm_set_variant.argtypes = [H, ctypes.c_int]
         L.dbm_autotune.argtypes = [H, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
@@ -238,6 +239,11 @@ def dbm_launch_info(h) -> dict:
     _check(lib().dbm_launch_info(h, *[ctypes.byref(v) for v in vals]), "dbm_launch_info")
     return dict(zip(("grid", "threads", "smem_bytes", "rows_per_item", "items", "variant"),
                     [v.value for v in vals]))
+
+
+def dbm_selftest_wait(dev_status_ptr: int, arrive: bool, limit_cycles: int, stream=None):
+    _check(lib().dbm_selftest_wait(ctypes.c_void_p(dev_status_ptr), int(bool(arrive)), int(limit_cycles),
+                                   _stream(stream)), "dbm_selftest_wait")
 
 
 def dbm_num_variants(precision: int) -> int:

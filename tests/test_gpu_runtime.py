@@ -144,3 +144,26 @@ def test_fp32_reciprocal_is_within_one_ulp_of_ieee():
     torch.cuda.synchronize()
     ulp = (a.view(torch.int32).long() - b.view(torch.int32).long()).abs()
     assert int(ulp.max()) <= 1
+
+
+def test_bounded_wait_runs_out_reports_and_leaves_the_context_usable():
+    """The device waits of the step kernels give up after a cycle limit: a
+    wait on an mbarrier that nothing arrives on ends after 2^22 cycles (about
+    2 ms) with the timeout bit set, the context still runs kernels, and the
+    same wait with an arrival completes without it."""
+    import torch
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    dbm.dbm_selftest_wait(st.data_ptr(), False, 1 << 22)        # nothing arrives
+    dbm.dbm_selftest_wait(st.data_ptr() + 4, True, 1 << 22)     # warp 1 arrives
+    torch.cuda.synchronize()
+    assert st.tolist() == [1, 0]
+    # the context is intact: a step runs and is finite
+    w = W.explosion(64, 32, nsteps=0, seed=3)
+    out = dbm.Simulation(dict(w.params, precision="fp32"))
+    out.init_state(w.fields)
+    out.step(5)
+    m = out.moments()
+    assert np.isfinite(m["rho"]).all() and dbm.dbm_status(out.h) == dbm.DBM_OK
+    out.close()
+    with pytest.raises(Exception):
+        dbm.dbm_selftest_wait(st.data_ptr(), False, 0)          # invalid limit
