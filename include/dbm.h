@@ -57,6 +57,8 @@ extern "C" {
 #define DBM_ECUDA       8  /* a CUDA runtime call failed                           */
 #define DBM_ECANCELLED  9  /* request cancelled before it finished                 */
 #define DBM_ENOTFOUND  10  /* unknown ticket                                       */
+#define DBM_EDEVICE    11  /* a device-side self-check failed: shared-memory layout,
+                              or (DBM_DEBUG builds) a copy or store out of bounds   */
 
 #define DBM_NV 33          /* D2V33: 1 rest + 4 rings x 8 directions (Sec. II.B)  */
 
@@ -195,7 +197,9 @@ int dbm_noneq_device(dbm_t *h, double *d_out, void *stream);
 int64_t dbm_steps_done(const dbm_t *h);
 
 /* Synchronise `stream` and report the sticky device status word: DBM_OK,
- * DBM_ETIMEOUT (a bounded wait in a step kernel expired) or DBM_ECUDA. */
+ * DBM_ETIMEOUT (a bounded wait in a step kernel expired), DBM_EDEVICE (a
+ * device-side self-check failed and the step skipped the offending copy or
+ * store; dbm_last_error says which) or DBM_ECUDA. */
 int dbm_status(dbm_t *h, void *stream);
 
 /* Checkpoint: copy the raw state to host memory.  f receives 33 * ntheta * nr

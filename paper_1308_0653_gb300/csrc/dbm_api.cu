@@ -397,6 +397,22 @@ extern "C" {
 
 const char *dbm_version(void) { return "dbm-gb300 1.0 (sm_103a)"; }
 
+// Status bits of the device self-checks -> DBM_EDEVICE with a message.
+static int device_check_status(int status)
+{
+    if (status & ST_SMEM_ALIGN) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "step kernel: dynamic shared memory not 128-byte aligned, step skipped");
+        return DBM_EDEVICE;
+    }
+    if (status & ST_BOUNDS) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "step kernel (debug build): a copy or store out of bounds or misaligned was skipped");
+        return DBM_EDEVICE;
+    }
+    return DBM_OK;
+}
+
 const char *dbm_strerror(int status)
 {
     switch (status) {
@@ -411,6 +427,7 @@ const char *dbm_strerror(int status)
     case DBM_ECUDA: return g_last_error[0] ? g_last_error : "CUDA error";
     case DBM_ECANCELLED: return "cancelled";
     case DBM_ENOTFOUND: return "unknown ticket";
+    case DBM_EDEVICE: return "device-side self-check failed";
     default: return "unknown status";
     }
 }
@@ -780,6 +797,7 @@ int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, doubl
     CK(cudaMemcpyAsync(&status, h->buf + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (status & ST_WAIT_TIMEOUT) return DBM_ETIMEOUT;
+    if (device_check_status(status) != DBM_OK) return DBM_EDEVICE;
     if (status & ST_NONFINITE) {
         CK(cudaMemsetAsync(h->buf + h->L.status, 0, sizeof(int), s));
         CK(cudaStreamSynchronize(s));
@@ -798,7 +816,7 @@ int dbm_status(dbm_t *h, void *stream)
     CK(cudaMemcpyAsync(&status, h->buf + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (status & ST_WAIT_TIMEOUT) return DBM_ETIMEOUT;
-    return DBM_OK;
+    return device_check_status(status);
 }
 
 int dbm_export_state(dbm_t *h, void *f, void *lam, int64_t *steps, void *stream)

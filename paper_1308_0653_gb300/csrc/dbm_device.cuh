@@ -32,6 +32,23 @@ constexpr int NARR = 34;  // 33 f planes + lambda
 constexpr int ST_WAIT_TIMEOUT = 1;   // an mbarrier wait gave up
 constexpr int ST_NONFINITE = 2;      // a moment was NaN / inf (moments kernel)
 constexpr int ST_SMEM_ALIGN = 4;     // dynamic shared memory not 128-byte aligned (step skipped)
+constexpr int ST_BOUNDS = 8;         // DBM_DEBUG builds: a copy or store failed its bounds check
+
+// DBM_DEBUG builds check every copy the producer issues (tensor coordinates on
+// the 16-byte boundary TMA requires, rows inside the grid, bulk extents inside
+// the row and 16-byte aligned) and every global store of the update, and skip
+// a failing one with ST_BOUNDS set; a skipped copy ends the step through the
+// abort path, like an expired wait.  Release builds compile the checks out.
+#ifdef DBM_DEBUG
+#define DBM_DEBUG_CHECK(cond, status_ptr) (dbm::debug_check((cond), (status_ptr)))
+#else
+#define DBM_DEBUG_CHECK(cond, status_ptr) (true)
+#endif
+__device__ __forceinline__ bool debug_check(bool ok, int *status)
+{
+    if (!ok) atomicOr(status, ST_BOUNDS);
+    return ok;
+}
 
 template <typename real> struct Halo;
 template <> struct Halo<float> { static constexpr int value = 4; };   // 16 bytes
@@ -259,6 +276,8 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     using O = Op<real>;
     const real H = real(0.70710678118654752440);  // cos(pi/4)
     const real one = real(1), half = real(0.5);
+    // the site's stores stay inside its instance's planes
+    if (!DBM_DEBUG_CHECK(j >= 0 && j < A.nr && A.nr <= A.ld && m >= 0 && m < A.ntheta, A.status)) return;
 
     // --- a1: load the site's 33 f and lambda -------------------------------
     real f[NV];
@@ -372,6 +391,16 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
             tn[i] = col + to_prev + (wrap_prev ? (((i + 1) & 7) - i) * WP : 0);
         else
             tn[i] = col + to_next + (wrap_next ? (((i + 7) & 7) - i) * WP : 0);
+#ifdef DBM_DEBUG
+        {
+            // velocity planes q = 1 + i .. 25 + i of direction i: neighbour
+            // reads stay inside the 33 planes of their row buffer
+            const int tr = tn[i] - (sn8[i] >= real(0) ? to_prev : to_next);
+            const bool ok = (1 + i) * WP + rn[i] >= 0 && (25 + i) * WP + rn[i] < NV * WP &&
+                            (1 + i) * WP + tr >= 0 && (25 + i) * WP + tr < NV * WP;
+            if (!DBM_DEBUG_CHECK(ok, A.status)) return;
+        }
+#endif
     }
 
     // --- a7 + a11: update all velocities and store ------------------------
@@ -409,6 +438,7 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
     // transport acts on the stored variable alike (y - y_nb = lambda_nb - lambda);
     // the reaction step adds dlam to lambda, so it is taken off y
+    if (!DBM_DEBUG_CHECK(col + orr >= 0 && col + orr < WP, A.status)) return;
     const real lr = sc[LAMOFF + col + orr];
     const real lt = (uth >= real(0) ? sp : sn)[LAMOFF + col];
     real ln = kY ? O::sub(lst, dlam) : O::add(lst, dlam);
@@ -756,6 +786,25 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
             const int nth = pa->ntheta;
             m = m < 0 ? m + nth : (m >= nth ? m - nth : m);
             real *buf = sm + slot * SLOT;
+#ifdef DBM_DEBUG
+            {
+                // the row is in the grid; the strip starts inside the row; a tensor
+                // box's first column is on a 16-byte boundary; bulk extents are
+                // inside the padded row and multiples of 16 bytes
+                const int jlo = max(pj0 - HALO, 0), jhi = min(pj0 + W + HALO, pa->ld);
+                bool ok = m >= 0 && m < nth && pj0 >= 0 && pj0 < pa->nr && pa->nr <= pa->ld;
+                if (TMAP) ok = ok && ((pj0 - HALO) * (int)sizeof(real)) % 16 == 0;
+                else ok = ok && jhi > jlo && ((jhi - jlo) * (int)sizeof(real)) % 16 == 0 &&
+                          (((long long)m * pa->ld + jlo) * (long long)sizeof(real)) % 16 == 0;
+                if (!ok) {  // uniform over the warp: every input is
+                    if (lane == 0) {
+                        atomicOr(pa->status, ST_BOUNDS);
+                        abort_flag = 1;
+                    }
+                    break;
+                }
+            }
+#endif
             if constexpr (TMAP) {
                 // one 3-D tile (all 33 f planes of the strip's row), one 2-D tile
                 // (lambda), one bulk copy (trig row); the box starts at the

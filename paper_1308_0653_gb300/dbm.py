@@ -16,7 +16,7 @@ from . import build as _build
 
 NV = 33
 DBM_OK, DBM_EINVAL, DBM_ECFL, DBM_ENOMEM, DBM_EBUSY, DBM_ENOTREADY = 0, 1, 2, 3, 4, 5
-DBM_ETIMEOUT, DBM_ENONFINITE, DBM_ECUDA, DBM_ECANCELLED, DBM_ENOTFOUND = 6, 7, 8, 9, 10
+DBM_ETIMEOUT, DBM_ENONFINITE, DBM_ECUDA, DBM_ECANCELLED, DBM_ENOTFOUND, DBM_EDEVICE = 6, 7, 8, 9, 10, 11
 DBM_FP32, DBM_FP64 = 0, 1
 DBM_BC_OUTFLOW, DBM_BC_CENTRE = 0, 1
 DBM_R_EXPLICIT, DBM_R_CONSISTENT = 0, 1
@@ -50,7 +50,7 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if _build.debug_requested() else _build.LIB
 
 
 def lib():
