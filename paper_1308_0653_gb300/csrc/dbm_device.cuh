@@ -905,11 +905,17 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                     reinterpret_cast<int *>(dst)[q] = reinterpret_cast<const int *>(ga)[q];
                 named_bar_sync(1, W);
                 parity ^= 1;
-                // and from there into registers for the item: the update reads
-                // about 40 of them per site, which a single instance takes from
-                // the constant bank as instruction operands
-                const StepArgs<real> Areg = *dst;
-                run_item(Areg, j0, mb, me);
+                // and (FP32) from there into registers for the item: the update
+                // reads about 40 of them per site, which a single instance takes
+                // from the constant bank as instruction operands.  FP64 is bound
+                // by its arithmetic pipe and short of registers: it reads them
+                // from shared memory.
+                if constexpr (sizeof(real) == 4) {
+                    const StepArgs<real> Areg = *dst;
+                    run_item(Areg, j0, mb, me);
+                } else {
+                    run_item(*dst, j0, mb, me);
+                }
             } else {
                 run_item(*ga, j0, mb, me);
             }
