@@ -49,14 +49,16 @@ def test_reactive_explosion_512_full(orc, precision):
     assert_close(out, ref, TOL[precision], f"explosion512 {precision}")
 
 
-def test_implosion_2048_in_bench_launch_shape(orc):
-    """2048 x 2048 reactive implosion, FP32, 4 steps, in the launch shape the
-    benchmark times (automatic rows per item, persistent grid)."""
-    w = W.implosion(2048, 2048, nsteps=4, seed=0)
+@pytest.mark.parametrize("omega1", [1.0, 2.0, 4.0])
+def test_implosion_2048_in_bench_launch_shape(orc, omega1):
+    """2048 x 2048 reactive implosion, FP32, 20 steps, for each of the rate
+    constants omega1 in {1, 2, 4} of the workload definition, in the launch
+    shape the benchmark times (automatic rows per item, persistent grid)."""
+    w = W.implosion(2048, 2048, nsteps=20, seed=0, omega1=omega1)
     ref = run_oracle(orc, w)
     out = run_gpu(w, "fp32")
     assert out["launch"]["threads"] in (128, 160) and out["launch"]["grid"] == 304
-    assert_close(out, ref, TOL["fp32"], "implosion2048 fp32")
+    assert_close(out, ref, TOL["fp32"], f"implosion2048 omega1={omega1:g} fp32")
 
 
 @pytest.mark.parametrize("nr,nth,rows", [(1, 8, 0), (5, 3, 0), (100, 7, 0), (130, 16, 1),
