@@ -449,12 +449,12 @@ def run_batch(args):
     b = dbm.Batch(len(ws), 1 << 22, precision="fp32", rows_per_item=args.rows_per_item)
     tune_steps = 64
     for k, s in enumerate(sims):
-        b.attach(k, s, args.batch_steps + 6 * (32 + tune_steps))
+        b.attach(k, s, args.batch_steps + 8 * (32 + tune_steps))
     tune = None
     if args.rows_per_item == 0:
         # batch autotuner on the live batch: kernel x rows per item
         v, r, ms = b.autotune(steps=tune_steps, stream=stream)
-        names = [f"v{vv}/r{rr}" for vv in (4, 2) for rr in (16, 32, 64)]
+        names = [f"v{vv}/r{rr}" for vv in (4, 2) for rr in (16, 32, 64, "scaled")]
         tune = {"variant": v, "rows_per_item": r,
                 "ms_per_step": {n: round(x, 4) for n, x in zip(names, ms) if x > 0}}
     b.step(args.warmup, stream=stream)

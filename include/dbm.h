@@ -303,7 +303,8 @@ typedef struct dbm_batch_s dbm_batch_t;
 size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
 
 /* Create a batch on caller device memory (256-byte aligned, >=
- * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16).
+ * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16; -1 =
+ * scaled to each simulation: 16 up to 512 theta rows, 32 up to 1024, else 64).
  * Allocates a pinned host staging buffer for the tables.  Synchronous.
  * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
 int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
@@ -342,14 +343,15 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream);
 int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
 
 /* Autotuner of a batch: times the precision's default kernel and the
- * bulk-copy kernel, each with 16, 32 and 64 theta rows per work item, for
- * `steps` batched steps each (after 32 untimed steps) with CUDA
- * events on `stream`, and keeps the fastest.  The trials advance every
- * attached simulation (6 x (32 + steps) steps at most); attach them with
+ * bulk-copy kernel, each with 16, 32, 64 and size-scaled (-1) theta rows per
+ * work item, for `steps` batched steps each (after 32 untimed steps) with
+ * CUDA events on `stream`, and keeps the fastest.  The trials advance every
+ * attached simulation (8 x (32 + steps) steps at most); attach them with
  * enough steps left.  *variant and *rows_per_item receive the choice;
- * ms_per_step[6] (may be NULL) the time per step of each candidate in the
- * order (default, 16), (default, 32), (default, 64), (bulk, 16), (bulk, 32),
- * (bulk, 64); 0 for a candidate not run.  Errors: DBM_EINVAL, DBM_ECUDA. */
+ * ms_per_step[8] (may be NULL) the time per step of each candidate in the
+ * order (default, 16), (default, 32), (default, 64), (default, -1), then the
+ * same for the bulk-copy kernel; 0 for a candidate not run.
+ * Errors: DBM_EINVAL, DBM_ECUDA. */
 int dbm_batch_autotune(dbm_batch_t *b, int steps, void *stream, int *variant, int *rows_per_item,
                        float *ms_per_step);
 
@@ -382,7 +384,7 @@ typedef struct dbm_server_config {
     int32_t quantum;        /* steps per scheduling round (32 | quantum: graphs)   */
     int32_t precision;      /* DBM_FP32 or DBM_FP64, shared by all requests        */
     int64_t max_items;      /* capacity of the batch's work-item table             */
-    int32_t rows_per_item;  /* theta rows per work item (0 = 16)                   */
+    int32_t rows_per_item;  /* theta rows per work item (0 = 16, -1 = size-scaled) */
     int32_t max_bypass;     /* how often a queued request may be passed over       */
 } dbm_server_config;
 

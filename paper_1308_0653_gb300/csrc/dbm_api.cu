@@ -990,6 +990,18 @@ struct BatchLayout {
     size_t slot_bytes, slots, items, nitems, T, total;
 };
 
+// Theta rows per work item of one attached simulation: the batch's setting,
+// or with rows_per_item = -1 scaled to the simulation's size (16 up to 512
+// rows, 32 up to 1024, else 64): long items carry fewer halo rows per row
+// computed, short ones balance better.
+int batch_rows(const dbm_batch_t *b, const dbm_params &p)
+{
+    if (b->rows_per_item > 0) return b->rows_per_item;
+    int L = 16;
+    while (L < 64 && L * 32 < p.ntheta) L *= 2;
+    return L;
+}
+
 BatchLayout batch_layout(int max_slots, long long max_items, int precision)
 {
     BatchLayout L;
@@ -1149,7 +1161,7 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
                      void *dev_buf, size_t dev_bytes, dbm_batch_t **out)
 {
     if (!out || !dev_buf || max_slots < 1 || max_items < 1 || max_items > (1LL << 31) ||
-        rows_per_item < 0 || (precision != DBM_FP32 && precision != DBM_FP64))
+        rows_per_item < -1 || (precision != DBM_FP32 && precision != DBM_FP64))
         return DBM_EINVAL;
     *out = nullptr;
     if (((uintptr_t)dev_buf & 255) != 0) return DBM_EINVAL;
@@ -1160,7 +1172,7 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
     b->precision = precision;
     b->max_slots = max_slots;
     b->max_items = max_items;
-    b->rows_per_item = rows_per_item > 0 ? rows_per_item : 16;
+    b->rows_per_item = rows_per_item != 0 ? rows_per_item : 16;
     b->buf = static_cast<unsigned char *>(dev_buf);
     b->bytes = dev_bytes;
     b->off_slots = L.slots;
@@ -1275,7 +1287,8 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
         if (!b->inst[s]) continue;
         const dbm_params &p = b->inst[s]->p;
         const long long strips = (p.nr + b->ki.W - 1) / b->ki.W;
-        const long long segs = (p.ntheta + b->rows_per_item - 1) / b->rows_per_item;
+        const int L = batch_rows(b, p);
+        const long long segs = (p.ntheta + L - 1) / L;
         n += strips * segs;
     }
     if (n > b->max_items) return DBM_ENOMEM;
@@ -1296,8 +1309,8 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
     for (int s = 0; s < b->max_slots; ++s) {
         if (!b->inst[s]) continue;
         const dbm_params &p = b->inst[s]->p;
-        count[s] = (long long)((p.nr + b->ki.W - 1) / b->ki.W) *
-                   ((p.ntheta + b->rows_per_item - 1) / b->rows_per_item);
+        const int L = batch_rows(b, p);
+        count[s] = (long long)((p.nr + b->ki.W - 1) / b->ki.W) * ((p.ntheta + L - 1) / L);
     }
     long long k = 0;
     bool more = true;
@@ -1309,8 +1322,9 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
             const int strips = (p.nr + b->ki.W - 1) / b->ki.W;
             const long long it = cursor[s]++;
             const int strip = (int)(it % strips), seg = (int)(it / strips);
-            const int mb = seg * b->rows_per_item;
-            items[k++] = make_int4(s, strip * b->ki.W, mb, std::min(mb + b->rows_per_item, p.ntheta));
+            const int L = batch_rows(b, p);
+            const int mb = seg * L;
+            items[k++] = make_int4(s, strip * b->ki.W, mb, std::min(mb + L, p.ntheta));
             more = true;
         }
     }
@@ -1374,16 +1388,16 @@ int dbm_batch_autotune(dbm_batch_t *b, int steps, void *stream, int *variant, in
     const int vdef = b->precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
     const int vfb = b->precision == DBM_FP64 ? fallback_variant<double>() : fallback_variant<float>();
     const int vs[2] = {vdef, vfb};
-    const int rows[3] = {16, 32, 64};
+    const int rows[4] = {16, 32, 64, -1};  // -1: scaled to each simulation's size
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     int rc = DBM_OK, bestv = 0, bestr = 0;
     float bestms = 0.f;
-    for (int c = 0; c < 6 && rc == DBM_OK; ++c) {
-        const int v = vs[c / 3], r = rows[c % 3];
+    for (int c = 0; c < 8 && rc == DBM_OK; ++c) {
+        const int v = vs[c / 4], r = rows[c % 4];
         if (ms_per_step) ms_per_step[c] = 0.f;
-        if (c >= 3 && vfb == vdef) continue;
+        if (c >= 4 && vfb == vdef) continue;
         b->forced_variant = v;
         b->rows_per_item = r;
         b->dirty = true;

@@ -241,6 +241,50 @@ template <> struct Op<double> {
 };
 
 // ---------------------------------------------------------------------------
+// Unbiased rounding of the FP32 reaction variable.  Lambda grows by small
+// amounts per step (1e-5 is typical), a few hundred float ulps, and rounding
+// each new value to nearest drops the same fraction of an ulp step after step
+// while that amount changes slowly: over 20 000 steps of the 2048^2 implosion
+// that bias alone left lambda 1.7e-4 behind FP64.  The update is therefore
+// summed exactly (TwoSum, Knuth) and rounded to one of the two floats around
+// the exact value with probability given by the distance (stochastic
+// rounding), which has no bias.  The uniform number comes from a hash of the
+// site index and the site's previous value, so the result is a deterministic
+// function of the state: identical in every kernel variant, batch and replay.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// 32-bit integer hash (C. Wellons' "lowbias32"): a bijection with full avalanche.
+__device__ __forceinline__ uint32_t hash32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// s + e (|e| below a few ulps of s) rounded to a neighbouring float: towards
+// the exact value's far neighbour with probability |residual| / ulp, u in [0, 1).
+// Values outside (0, 1) are returned rounded to nearest (they are clamped next).
+__device__ __forceinline__ float round_stochastic_unit(float s, float e, float u)
+{
+    const float y = __fadd_rn(s, e);
+    if (!(y > 0.f && y < 1.f)) return y;
+    const float r = __fadd_rn(__fsub_rn(s, y), e);  // s - y is exact (y is within an ulp of s)
+    if (r == 0.f) return y;
+    const float other = __int_as_float(__float_as_int(y) + (r > 0.f ? 1 : -1));
+    const float gap = fabsf(__fsub_rn(other, y));     // one ulp, exact
+    return fabsf(r) > __fmul_rn(u, gap) ? other : y;
+}
+
+// ---------------------------------------------------------------------------
 // Stored reaction variable.  FP64 stores lambda itself.  FP32 stores the
 // unburnt fraction y = 1 - lambda: as lambda -> 1 the reaction increments per
 // step fall below half the spacing of floats just under 1 (6e-8) and would
@@ -441,9 +485,25 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     if (!DBM_DEBUG_CHECK(col + orr >= 0 && col + orr < WP, A.status)) return;
     const real lr = sc[LAMOFF + col + orr];
     const real lt = (uth >= real(0) ? sp : sn)[LAMOFF + col];
-    real ln = kY ? O::sub(lst, dlam) : O::add(lst, dlam);
-    ln = O::sub(ln, O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lst, lr)));
-    ln = O::sub(ln, O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lst, lt)));
+    const real tr = O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lst, lr));
+    const real tt = O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lst, lt));
+    real ln;
+    if constexpr (sizeof(real) == 4) {
+        // y - dlam - tr - tt summed exactly, then rounded without bias
+        float sum, err, e2;
+        two_sum_f(lst, -dlam, sum, err);
+        two_sum_f(sum, -tr, sum, e2);
+        err = __fadd_rn(err, e2);
+        two_sum_f(sum, -tt, sum, e2);
+        err = __fadd_rn(err, e2);
+        const uint32_t site = (uint32_t)m * (uint32_t)A.ld + (uint32_t)j;
+        const float u = (float)(hash32(site * 0x9e3779b9u ^ __float_as_uint(lst)) >> 8) * 0x1p-24f;
+        ln = round_stochastic_unit(sum, err, u);
+    } else {
+        ln = kY ? O::sub(lst, dlam) : O::add(lst, dlam);
+        ln = O::sub(ln, tr);
+        ln = O::sub(ln, tt);
+    }
     ln = fmin(fmax(ln, real(0)), real(1));
     A.lam_out[(long long)m * A.ld + j] = ln;
 }

@@ -305,7 +305,7 @@ def dbm_batch_step(b, nsteps, stream=None):
 def dbm_batch_autotune(b, steps: int, stream=None):
     """Returns (variant, rows_per_item, {(variant, rows): ms per step})."""
     v, r = ctypes.c_int(0), ctypes.c_int(0)
-    ms = (ctypes.c_float * 6)()
+    ms = (ctypes.c_float * 8)()
     _check(lib().dbm_batch_autotune(b, int(steps), _stream(stream), ctypes.byref(v), ctypes.byref(r), ms),
            "dbm_batch_autotune")
     return v.value, r.value, list(ms)
