@@ -449,7 +449,7 @@ def run_batch(args):
     b = dbm.Batch(len(ws), 1 << 22, precision="fp32", rows_per_item=args.rows_per_item)
     tune_steps = 64
     for k, s in enumerate(sims):
-        b.attach(k, s, args.batch_steps + 8 * (32 + tune_steps))
+        b.attach(k, s, args.batch_steps + 8 * (32 + 2 * tune_steps))
     tune = None
     if args.rows_per_item == 0:
         # batch autotuner on the live batch: kernel x rows per item

@@ -344,10 +344,10 @@ int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream);
 
 /* Autotuner of a batch: times the precision's default kernel and the
  * bulk-copy kernel, each with 16, 32, 64 and size-scaled (-1) theta rows per
- * work item, for `steps` batched steps each (after 32 untimed steps) with
- * CUDA events on `stream`, and keeps the fastest.  The trials advance every
- * attached simulation (8 x (32 + steps) steps at most); attach them with
- * enough steps left.  *variant and *rows_per_item receive the choice;
+ * work item, for twice `steps` batched steps each (after 32 untimed steps;
+ * the better of the two timings counts) with CUDA events on `stream`, and
+ * keeps the fastest.  The trials advance every attached simulation
+ * (8 x (32 + 2 steps) steps at most); attach them with enough steps left.  *variant and *rows_per_item receive the choice;
  * ms_per_step[8] (may be NULL) the time per step of each candidate in the
  * order (default, 16), (default, 32), (default, 64), (default, -1), then the
  * same for the bulk-copy kernel; 0 for a candidate not run.

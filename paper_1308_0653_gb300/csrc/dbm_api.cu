@@ -1404,18 +1404,23 @@ int dbm_batch_autotune(dbm_batch_t *b, int steps, void *stream, int *variant, in
         rc = dbm_batch_step(b, GRAPH_STEPS, stream);  // commit, graph capture, warm-up
         if (rc != DBM_OK) break;
         if (b->variant != v) continue;  // the tensor-map kernel is not usable for this batch
-        cudaEventRecord(e0, st);
-        rc = dbm_batch_step(b, steps, stream);
-        cudaEventRecord(e1, st);
-        if (rc != DBM_OK) break;
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "batch autotune timing");
-            break;
-        }
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= steps;
+        for (int rep = 0; rep < 2 && rc == DBM_OK; ++rep) {  // the better of two timings
+            cudaEventRecord(e0, st);
+            rc = dbm_batch_step(b, steps, stream);
+            cudaEventRecord(e1, st);
+            if (rc != DBM_OK) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "batch autotune timing");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            t /= steps;
+            if (rep == 0 || t < ms) ms = t;
+        }
+        if (rc != DBM_OK) break;
         if (ms_per_step) ms_per_step[c] = ms;
         if (bestv == 0 || ms < bestms) {
             bestv = v;

@@ -13,10 +13,12 @@
 // sites (one per thread) of a run of theta rows ("work item") and marches down
 // the rows.  A ring of NSTAGE shared-memory row buffers, each holding all 33
 // f planes plus lambda for the strip and a 16-byte halo on both radial sides,
-// is filled by TMA bulk copies (cp.async.bulk, completion on an mbarrier per
-// buffer).  Row m is computed from buffers m-1, m, m+1, so every f value is
-// read from HBM once per step (plus the halo columns and two halo rows per
-// item) and written once.
+// is filled by TMA (tensor-map tiles, cp.async.bulk.tensor, in the default
+// variant; per-array cp.async.bulk in the others), completion on an mbarrier
+// per buffer.  Row m is computed from buffers m-1, m, m+1, so every f value
+// is read from HBM once per step (plus the halo columns and two halo rows per
+// item) and written once.  Variant v1 (march) uses one CTA-wide barrier per
+// row; v2/v3 (march2) a producer warp and full/empty mbarriers.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (type only; descriptors are encoded by the host runtime)

@@ -142,7 +142,7 @@ def test_batch_autotune_picks_a_kernel_and_keeps_the_update():
     assert (info["variant"], info["rows_per_item"]) == (v, r)
     b.step(10)
     n = b.time()
-    assert 10 < n <= 8 * (32 + 8) + 10
+    assert 10 < n <= 8 * (32 + 2 * 8) + 10
     for s, w in zip(sims, ws):
         assert dbm.dbm_steps_done(s.h) == n
         got = s.export_state()
