@@ -2,11 +2,12 @@
 the release library and once with the checked one (DBM_DEBUG=1): ragged and
 degenerate grids, a disc sector, a batch of uneven simulations, FP32 and FP64.
 Writes every final state and status to the .npz file given as argument."""
+import os
 import sys
 
 import numpy as np
 
-sys.path.insert(0, __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__))))
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 from paper_1308_0653_gb300 import dbm  # noqa: E402
 from paper_1308_0653_gb300 import workloads as W  # noqa: E402
