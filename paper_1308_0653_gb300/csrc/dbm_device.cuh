@@ -460,11 +460,9 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
         const real rF = O::mul(rho, F[k]);
         const real beta = O::mul(rF, O::fma(O::mul(dtQR, O::add(A.v2[k], u2m2T)), half_inv_T2, A.one_m_decay));
         const real gamma = O::mul(rF, gam);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        // one velocity given its xi and the equilibrium polynomial at xi
+        auto update_one = [&](int i, real xi, real poly) {
             const int q = 1 + 8 * k + i;
-            const real xi = O::mul(vk, w[i]);
-            const real poly = O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0);
             real t = O::mul(poly, O::fma(-gamma, xi, beta));
             // REREAD: take f from shared memory again instead of holding all
             // 33 values in registers across the moment pass (fewer registers)
@@ -473,6 +471,26 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
             const real adv = O::fma(ar[i], sc[q * WP + rn[i]], O::mul(at[i], sc[q * WP + tn[i]]));
             t = O::fma(vk, adv, t);
             out[(long long)q * A.plane] = t;
+        };
+        if constexpr (sizeof(real) == 8) {
+            // FP64 is bound by its arithmetic: opposite directions i and i+4
+            // have xi and -xi, so the polynomial splits into an even part E
+            // and an odd part O evaluated once, poly(+-xi) = E +- O
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const real xi = O::mul(vk, w[i]);
+                const real x2 = O::mul(xi, xi);
+                const real Ev = O::fma(x2, O::fma(x2, real(1.0 / 24.0), A2), A0);
+                const real Od = O::mul(xi, O::fma(x2, real(1.0 / 6.0), A1));
+                update_one(i, xi, O::add(Ev, Od));
+                update_one(i + 4, -xi, O::sub(Ev, Od));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const real xi = O::mul(vk, w[i]);
+                update_one(i, xi, O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0));
+            }
         }
     }
 
