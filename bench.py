@@ -89,6 +89,8 @@ def parse():
                     help="theta rows per work item of batches and the server (0 = library default)")
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--max-queue", type=int, default=1000,
+                    help="server queue bound (requests beyond it are refused and counted)")
     ap.add_argument("--duration", type=float, default=60.0)
     ap.add_argument("--smax", type=int, default=20000)
     ap.add_argument("--batch-nmin", type=int, default=128, help="smallest side of a batch instance")
@@ -509,23 +511,37 @@ def run_serve(args):
     torch.cuda.set_device(0)
     free, total = torch.cuda.mem_get_info()
     pool = int(min(free * 0.8, 150e9))
-    srv = dbm.Server(pool_bytes=pool, max_slots=64, max_queue=100000, quantum=64,
+    # The server copies each request's initial fields until it is admitted, so
+    # the queue is bounded (max_queue, requests beyond it are refused with
+    # DBM_EBUSY and counted): under sustained overload an unbounded queue grows
+    # by ~30 MB of host memory per request.
+    srv = dbm.Server(pool_bytes=pool, max_slots=64, max_queue=args.max_queue, quantum=64,
                      max_items=1 << 20, rows_per_item=args.rows_per_item)
     arr = W.arrivals(args.rate, args.duration, seed=0)
     t0 = time.perf_counter()
-    tickets = []
+    tickets = []   # (ticket, sites, steps): the fields are not kept here
+    offered = 0.0
+    refused = 0
     for k, ta in enumerate(arr):
         w = W.serving_request(k, seed=0, nmax=args.nmax, smax=args.smax)
+        offered += w.sites * NV * w.nsteps
         while time.perf_counter() - t0 < ta:
             time.sleep(0.001)
-        tickets.append((srv.submit(dict(w.params, precision="fp32"), w.fields, w.nsteps), w))
+        try:
+            tickets.append((srv.submit(dict(w.params, precision="fp32"), w.fields, w.nsteps),
+                            w.sites, w.nsteps))
+        except dbm.DbmError as e:
+            if e.status != dbm.DBM_EBUSY:
+                raise
+            refused += 1
+        del w
     lat, upd = [], 0.0
-    for t, w in tickets:
+    for t, sites, _ in tickets:
         left = args.duration - (time.perf_counter() - t0)
         st, res = srv.poll(t, timeout_us=int(max(left, 0) * 1e6))
         if st == dbm.DBM_OK and res["status"] == dbm.DBM_OK:
             lat.append(res["t_end"] - res["t_submit"])
-            upd += w.sites * NV * res["steps"]
+            upd += sites * NV * res["steps"]
     wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
@@ -537,14 +553,15 @@ def run_serve(args):
             "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, side "
                                    f"logU[128, {args.nmax}], steps logU[1000, {args.smax}], "
                                    "explosion/implosion 50/50, omega1 in {1, 2, 4}",
-                       "requests": len(tickets), "pool_bytes": pool, "max_slots": 64, "quantum": 64},
+                       "requests": len(arr), "accepted": len(tickets), "refused_queue_full": refused,
+                       "max_queue": args.max_queue, "pool_bytes": pool, "max_slots": 64, "quantum": 64},
             "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.nanpercentile(lat, 50)),
             "p99_s": float(np.nanpercentile(lat, 99)), "backlog": len(tickets) - int(np.isfinite(lat).sum()),
             "executed_glups": executed_glups,
             "single_instance": {"value": single, "unit": UNIT,
                                 "workload": "reactive implosion 2048x2048, 500 steps"},
             "executed_over_single_instance": executed_glups / single,
-            "offered_glups": sum(w.sites * NV * w.nsteps for _, w in tickets) / args.duration / 1e9,
+            "offered_glups": offered / args.duration / 1e9,
             "server": stats}
     print(json.dumps(line), flush=True)
     return 0
