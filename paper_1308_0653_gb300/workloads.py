@@ -55,6 +55,13 @@ def uniform(seed: int, stream: int, n: int) -> np.ndarray:
     return (splitmix64(seed, stream, n) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
+def uniform_at(seed: int, stream: int, i: int) -> float:
+    """The i-th value (from 0) of uniform(seed, stream, .), computed alone."""
+    key = int(_mix64(np.array([(seed * _GOLDEN + stream + 1) & _MASK], dtype=np.uint64))[0])
+    x = np.array([(key + (i + 1) * _GOLDEN) & _MASK], dtype=np.uint64)
+    return float((_mix64(x) >> np.uint64(11)).astype(np.float64)[0] * (2.0 ** -53))
+
+
 @dataclass
 class Workload:
     """Parameters (paper names) + initial fields + number of time steps."""
@@ -227,14 +234,13 @@ def batch(n_instances: int = 64, seed: int = 0, nsteps: int = 5000, nmin: int = 
 
 def arrivals(rate_hz: float, duration_s: float, seed: int = 0):
     """Poisson arrival times (exponential gaps, stream 30) within duration_s."""
-    t, out, i = 0.0, [], 0
+    n = max(16, int(rate_hz * duration_s * 1.5) + 16)
     while True:
-        u = uniform(seed, 30, i + 1)[-1]
-        t += -math.log(1.0 - u) / rate_hz
-        if t >= duration_s:
-            return out
-        out.append(t)
-        i += 1
+        gaps = -np.log1p(-uniform(seed, 30, n)) / rate_hz
+        t = np.cumsum(gaps)
+        if t[-1] >= duration_s:
+            return [float(x) for x in t[t < duration_s]]
+        n *= 2
 
 
 def serving_request(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
@@ -242,7 +248,7 @@ def serving_request(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
     """Request k of the serving stream: side N ~ logU[nmin, nmax] (stream 31,
     multiple of `align`), steps ~ logU[smin, smax] (stream 32), explosion or
     implosion with equal odds (stream 33), omega1 in {1, 2, 4} (stream 34)."""
-    u = [uniform(seed, 31 + s, k + 1)[-1] for s in range(4)]
+    u = [uniform_at(seed, 31 + s, k) for s in range(4)]
     N = int(nmin * (nmax / nmin) ** u[0])
     N = max(align, (N // align) * align)
     steps = int(smin * (smax / smin) ** u[1])
