@@ -360,6 +360,7 @@ void scheduler(dbm_server_t *S)
                 ++qseq;
                 enqueued = true;
                 S->stats.executed += work;
+                S->stats.batch_time = (double)dbm_batch_time(S->batch);  // read under the lock by stats
             } else {
                 S->fatal = rc;
             }
@@ -553,8 +554,7 @@ int dbm_server_stats_get(dbm_server_t *S, dbm_server_stats *out)
     std::lock_guard<std::mutex> lock(S->mu);
     *out = S->stats;
     out->pool_free_largest = (double)S->pool.largest();
-    out->batch_time = (double)dbm_batch_time(S->batch);
-    out->status = S->fatal;
+    out->status = S->fatal;  // batch_time: kept in S->stats by the scheduler thread
     return DBM_OK;
 }
 
