@@ -427,7 +427,15 @@ int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_
 /* Queue a simulation: params (precision must match the server's), initial
  * fields (copied before return), nsteps.  *ticket identifies it.
  * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (larger than the whole pool),
- * DBM_EBUSY (queue full). */
+ * DBM_EBUSY (queue full), or the error that ended the server's work.
+ *
+ * A batched step that fails (DBM_ECUDA, DBM_EDEVICE, ...) ends the server's
+ * work: nothing more is launched, and every queued or resident request whose
+ * steps are not all done finishes with that status and no arrays (the stats'
+ * status holds it).  Requests that finished before it keep their results.
+ * For tests of this path, DBM_SERVER_FAIL_QUANTUM=n in the environment at
+ * dbm_server_create makes quantum n (from 0) fail with DBM_ECUDA on the host,
+ * without a launch. */
 int dbm_submit(dbm_server_t *s, const dbm_params *p, const dbm_fields *init, int64_t nsteps,
                uint64_t *ticket);
 

@@ -129,7 +129,8 @@ struct dbm_server_s {
     std::thread th;
     std::chrono::steady_clock::time_point t0;
     dbm_server_stats stats;
-    int fatal = DBM_OK;
+    int fatal = DBM_OK;          // first error of a batched step; ends the server's work
+    int64_t fail_quantum = -1;   // fault injection: this quantum fails with DBM_ECUDA
 };
 
 namespace {
@@ -157,24 +158,28 @@ double *alloc_fields(size_t N)
 }
 
 // Retire a request whose slot was already detached and whose buffers no
-// launch touches any more: moments to host (unless cancelled), destroy, free
-// its pool block.  Scheduler thread, lock not held.
-void retire(dbm_server_t *S, Request *r, bool cancelled)
+// launch touches any more: moments to host (status DBM_OK), or no result
+// (DBM_ECANCELLED, or the server's fatal error), destroy, free its pool
+// block.  Scheduler thread, lock not held.
+void retire(dbm_server_t *S, Request *r, int status)
 {
-    int status = cancelled ? DBM_ECANCELLED : DBM_OK;
-    if (!cancelled) {
+    if (status == DBM_OK) {
         const size_t N = (size_t)r->p.nr * r->p.ntheta;
         double *host = alloc_fields(N);
         if (!host) {
             status = DBM_ENOMEM;
         } else {
-            r->res.rho = host;
-            r->res.ur = host + N;
-            r->res.uth = host + 2 * N;
-            r->res.T = host + 3 * N;
-            r->res.lam = host + 4 * N;
-            status = dbm_moments(r->h, r->res.rho, r->res.ur, r->res.uth, r->res.T, r->res.lam,
+            status = dbm_moments(r->h, host, host + N, host + 2 * N, host + 3 * N, host + 4 * N,
                                  r->res.totals, S->io);
+            if (status == DBM_OK || status == DBM_ENONFINITE) {
+                r->res.rho = host;
+                r->res.ur = host + N;
+                r->res.uth = host + 2 * N;
+                r->res.T = host + 3 * N;
+                r->res.lam = host + 4 * N;
+            } else {
+                std::free(host);
+            }
         }
     }
     r->res.steps = dbm_steps_done(r->h);
@@ -227,7 +232,10 @@ void admit(dbm_server_t *S, Request *r, int slot, size_t off, size_t bytes)
 // retired (moments, destroy, free) as soon as no launch in flight can touch
 // its buffers: at once if it ended before the running quantum starts, else
 // once that quantum is done.  A cancelled simulation is active in the running
-// quantum and waits for it the same way.
+// quantum and waits for it the same way.  If a batched step fails (a CUDA
+// error, a device self-check), the scheduler enqueues nothing more, waits for
+// the quanta in flight and ends every queued and resident request with that
+// error; later submissions are refused with it.
 void scheduler(dbm_server_t *S)
 {
     cudaSetDevice(S->device);
@@ -241,7 +249,7 @@ void scheduler(dbm_server_t *S)
     int64_t done_q = -1;   // every quantum up to this one is complete
     struct Deferred {
         Request *r;
-        bool cancelled;
+        int status;        // DBM_OK, DBM_ECANCELLED or the fatal error
         int64_t wait_q;    // retire once this quantum is complete
     };
     std::vector<Deferred> deferred;
@@ -272,9 +280,9 @@ void scheduler(dbm_server_t *S)
                 S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
             }
             for (auto it = S->queue.begin(); it != S->queue.end();) {  // cancelled while queued
-                if ((*it)->cancel) {
+                if ((*it)->cancel || S->fatal != DBM_OK) {
                     S->stats.queued -= 1;
-                    finish(S, *it, DBM_ECANCELLED);
+                    finish(S, *it, (*it)->cancel ? DBM_ECANCELLED : S->fatal);
                     it = S->queue.erase(it);
                 } else {
                     ++it;
@@ -324,9 +332,11 @@ void scheduler(dbm_server_t *S)
         const int64_t t_now = dbm_batch_time(S->batch);
         bool any_active = false;
         int64_t steps = S->cfg.quantum;
+        int fatal = DBM_OK;
         {
             std::lock_guard<std::mutex> lock(S->mu);
-            for (int k = 0; k < S->cfg.max_slots; ++k) {
+            fatal = S->fatal;
+            for (int k = 0; k < S->cfg.max_slots && fatal == DBM_OK; ++k) {
                 Request *r = S->slots[k];
                 if (!r || !r->h || r->state != RUNNING || r->leaving || r->cancel) continue;
                 const int64_t left = dbm_batch_remaining(S->batch, k);
@@ -350,7 +360,8 @@ void scheduler(dbm_server_t *S)
         if (any_active) {
             const int k = (int)(qseq & 1);
             wait_slot(k);  // quantum n-2: at most two in flight
-            const int rc = dbm_batch_step(S->batch, steps, S->compute);
+            const int rc = S->fail_quantum == qseq ? DBM_ECUDA  // host-side fault injection
+                                                   : dbm_batch_step(S->batch, steps, S->compute);
             std::lock_guard<std::mutex> lock(S->mu);
             if (rc == DBM_OK) {
                 cudaEventRecord(qdone[k], S->compute);
@@ -362,7 +373,7 @@ void scheduler(dbm_server_t *S)
                 S->stats.executed += work;
                 S->stats.batch_time = (double)dbm_batch_time(S->batch);  // read under the lock by stats
             } else {
-                S->fatal = rc;
+                S->fatal = fatal = rc;
             }
         }
 
@@ -377,12 +388,12 @@ void scheduler(dbm_server_t *S)
             }
 
         // ---- 4. retire what no launch in flight touches ------------------------
-        std::vector<std::pair<Request *, bool>> now;
+        std::vector<std::pair<Request *, int>> now;
         {
             std::vector<Deferred> keep;
             for (const Deferred &d : deferred) {
                 if (d.wait_q <= done_q)
-                    now.push_back({d.r, d.cancelled});
+                    now.push_back({d.r, d.status});  // its steps ran before any failure
                 else
                     keep.push_back(d);
             }
@@ -394,13 +405,14 @@ void scheduler(dbm_server_t *S)
                 Request *r = S->slots[k];
                 if (!r || !r->h || r->state != RUNNING || r->leaving) continue;
                 const bool finished = dbm_batch_remaining(S->batch, k) == 0;
-                if (!r->cancel && !finished) continue;
+                if (!r->cancel && !finished && fatal == DBM_OK) continue;
+                const int status = r->cancel ? DBM_ECANCELLED : finished ? DBM_OK : fatal;
                 r->leaving = true;
                 dbm_batch_detach(S->batch, k);  // out of the next quantum's tables
                 if (running_q < 0 || (!r->cancel && r->end_step <= running_from))
-                    now.push_back({r, r->cancel});
+                    now.push_back({r, status});
                 else
-                    deferred.push_back({r, r->cancel, running_q});
+                    deferred.push_back({r, status, running_q});
             }
         }
         for (auto &lr : now) retire(S, lr.first, lr.second);
@@ -436,6 +448,9 @@ int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_
     std::memset(&S->stats, 0, sizeof(S->stats));
     S->slots.assign(cfg->max_slots, nullptr);
     S->t0 = std::chrono::steady_clock::now();
+    // Host-side fault injection for tests of the failure path: quantum n
+    // (counted from 0) reports DBM_ECUDA instead of launching.
+    if (const char *env = std::getenv("DBM_SERVER_FAIL_QUANTUM")) S->fail_quantum = std::atoll(env);
     int rc = DBM_OK;
     if (cudaGetDevice(&S->device) != cudaSuccess) rc = DBM_ECUDA;
     if (rc == DBM_OK && cudaStreamCreateWithFlags(&S->compute, cudaStreamNonBlocking) != cudaSuccess)
@@ -488,6 +503,10 @@ int dbm_submit(dbm_server_t *S, const dbm_params *p, const dbm_fields *init, int
         if (S->stop) {
             delete r;
             return DBM_EINVAL;
+        }
+        if (S->fatal != DBM_OK) {
+            delete r;
+            return S->fatal;
         }
         if ((int64_t)S->queue.size() >= S->cfg.max_queue) {
             delete r;

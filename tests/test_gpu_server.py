@@ -103,3 +103,35 @@ def test_destroy_with_work_in_flight_cancels_it():
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 30
+
+
+def test_a_failed_batched_step_ends_every_unfinished_request_with_its_error(monkeypatch):
+    """Failure injected on the host: the third quantum reports DBM_ECUDA
+    instead of launching.  The request that finished in the first quantum
+    keeps its result (equal to running it alone); the resident and queued
+    ones end with DBM_ECUDA and no arrays, the server refuses new work with
+    that status, and it still shuts down."""
+    monkeypatch.setenv("DBM_SERVER_FAIL_QUANTUM", "2")
+    w = W.explosion(128, 128, nsteps=0, seed=24)
+    prm = dict(w.params, precision="fp32")
+    srv = dbm.Server(pool_bytes=1 << 28, max_slots=2, quantum=32)
+    monkeypatch.delenv("DBM_SERVER_FAIL_QUANTUM")
+    short = srv.submit(prm, w.fields, 32)            # all its steps are in quantum 0
+    others = [srv.submit(prm, w.fields, 100000) for _ in range(3)]
+    st, res = srv.poll(short, timeout_us=60_000_000)
+    assert st == dbm.DBM_OK and res["status"] == dbm.DBM_OK and res["steps"] == 32
+    ref = _alone(w, 32)
+    for k in dbm.FIELDS:
+        assert np.array_equal(res[k], ref[k]), k
+    for t in others:
+        st, res = srv.poll(t, timeout_us=60_000_000)
+        assert st == dbm.DBM_OK and res["status"] == dbm.DBM_ECUDA and res["rho"] is None
+    stats = srv.stats()
+    assert stats["status"] == dbm.DBM_ECUDA
+    assert (stats["completed"], stats["failed"], stats["running"], stats["queued"]) == (1, 3, 0, 0)
+    with pytest.raises(dbm.DbmError) as e:
+        srv.submit(prm, w.fields, 10)
+    assert e.value.status == dbm.DBM_ECUDA
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 30
