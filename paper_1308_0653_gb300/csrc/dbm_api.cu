@@ -340,8 +340,30 @@ int pick_variant(const dbm_params &p)
     return p.precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
 }
 
-// Launch shape for a kernel variant: persistent CTAs, one per resident slot;
-// theta rows per item chosen so the items fill the slots in one wave.
+// Theta rows per work item of one simulation.  The persistent CTAs take items
+// blockIdx.x, blockIdx.x + grid, ..., each item loading L + 2 rows (two halo
+// rows), so the busiest CTA handles ceil(items / slots) x (L + 2) rows.  Pick
+// the L that minimises it over the segment counts 1 .. ntheta (L = the
+// smallest rows per segment for that count); the fewest items on ties.
+int pick_rows_per_item(int ntheta, int strips, int slots)
+{
+    int best = ntheta;
+    long long best_cost = -1;
+    for (int segs = 1; segs <= ntheta; ++segs) {
+        const int L = (ntheta + segs - 1) / segs;
+        const long long items = (long long)strips * ((ntheta + L - 1) / L);
+        const long long cost = (items + slots - 1) / slots * (L + 2);
+        if (best_cost < 0 || cost < best_cost) {
+            best = L;
+            best_cost = cost;
+        }
+        if (L == 1) break;
+    }
+    return best;
+}
+
+// Launch shape for a kernel variant: persistent CTAs, one per resident slot,
+// and the rows per item above unless the parameters fix them.
 int configure_launch(dbm_t *h, int variant)
 {
     KernelInfo ki;
@@ -358,10 +380,7 @@ int configure_launch(dbm_t *h, int variant)
     const int slots = nsm * ki.blocks_per_sm;
     const int strips = (p.nr + ki.W - 1) / ki.W;
     int L_rows = p.rows_per_item;
-    if (L_rows == 0) {
-        const long long need = ((long long)p.ntheta * strips + slots - 1) / slots;
-        L_rows = (int)std::max(1LL, need);
-    }
+    if (L_rows == 0) L_rows = pick_rows_per_item(p.ntheta, strips, slots);
     L_rows = std::min(L_rows, p.ntheta);
     const KernelInfo old_ki = h->ki;
     h->ki = ki;

@@ -164,6 +164,53 @@ def test_every_kernel_variant_gives_the_same_bits(precision):
         assert np.array_equal(f, states[0][0]) and np.array_equal(lam, states[0][1])
 
 
+def _busiest_rows(ntheta, strips, slots, L):
+    """Rows the busiest persistent CTA loads: items are dealt round-robin and
+    each loads its L rows plus two halo rows."""
+    items = strips * -(-ntheta // L)
+    return -(-items // slots) * (L + 2)
+
+
+@pytest.mark.parametrize("precision,n", [("fp32", 1536), ("fp32", 2048), ("fp32", 3072),
+                                         ("fp64", 512), ("fp64", 2048)])
+def test_work_items_balance_the_persistent_grid(precision, n):
+    """The automatic rows per item leave the busiest CTA no more rows than
+    any other choice would (brute force over every L here).  A choice from
+    the average load alone, ceil(ntheta x strips / slots) rows, can give a
+    few more items than CTAs: on 2048^2 FP64 it gave 320 items to 304 CTAs,
+    so 16 of them ran two items and the step took twice the rows."""
+    import torch
+    from paper_1308_0653_gb300 import dbm
+    w = W.implosion(64, 64, nsteps=0, seed=0)
+    sim = dbm.Simulation(dict(w.params, nr=n, ntheta=n, precision=precision))
+    info = sim.launch_info()
+    sim.close()
+    slots = 2 * torch.cuda.get_device_properties(0).multi_processor_count  # 2 CTAs per SM
+    width = info["threads"] - 32                                           # producer warp + W sites
+    strips = -(-n // width)
+    L = info["rows_per_item"]
+    assert info["items"] == strips * -(-n // L) and info["grid"] == min(info["items"], slots)
+    best = min(_busiest_rows(n, strips, slots, c) for c in range(1, n + 1))
+    assert _busiest_rows(n, strips, slots, L) == best
+
+
+def test_work_items_in_several_waves_give_the_same_bits():
+    """1536^2 FP64 runs 600 work items of 62 rows on 304 CTAs (two waves);
+    one item per strip (1536 rows) gives the same bits."""
+    from paper_1308_0653_gb300 import dbm
+    w = W.explosion(1536, 1536, nsteps=0, seed=14)
+    states = []
+    for rows in (0, 1536):
+        sim = dbm.Simulation(dict(w.params, precision="fp64", rows_per_item=rows))
+        if rows == 0:
+            assert sim.launch_info()["items"] > sim.launch_info()["grid"]
+        sim.init_state(w.fields)
+        sim.step(3)
+        states.append(sim.export_state())
+        sim.close()
+    assert np.array_equal(states[0][0], states[1][0]) and np.array_equal(states[0][1], states[1][1])
+
+
 def test_autotune_picks_a_variant_and_keeps_the_update(orc):
     from paper_1308_0653_gb300 import dbm
     w = W.explosion(256, 64, nsteps=0, seed=13, dt=2e-5)
