@@ -129,6 +129,20 @@ int dbm_check(const dbm_params *p, double *cfl);
  * or 0 if *p is invalid. */
 size_t dbm_state_bytes(const dbm_params *p);
 
+/* Host-only: the work split of one simulation's step.  The grid is cut into
+ * strips of `width` radial sites (the kernel's W: dbm_launch_info's threads
+ * minus the producer warp's 32) by runs of *rows_per_item theta rows; the
+ * ceil(nr / width) x ceil(ntheta / rows) items are dealt round-robin to
+ * `slots` persistent CTAs (SMs x resident CTAs per SM), and each loads its
+ * rows plus two halo rows.  rows_requested > 0 fixes the rows (at most
+ * ntheta); 0 picks the rows that minimise the busiest CTA's loaded rows,
+ * ceil(items / slots) x (rows + 2), with the fewest items on ties.  This is
+ * the split dbm_create and dbm_set_variant use.  Writes *rows_per_item and
+ * *items (either may be NULL).  Errors: DBM_EINVAL (a size below 1 or a
+ * negative rows_requested). */
+int dbm_plan_items(int32_t nr, int32_t ntheta, int32_t width, int32_t slots, int32_t rows_requested,
+                   int32_t *rows_per_item, int64_t *items);
+
 /* Bind a simulation to caller device memory dev_buf (dev_bytes >=
  * dbm_state_bytes(p), 256-byte aligned, on the current device).  Uploads the
  * geometry tables and clears the buffer on the legacy default stream and

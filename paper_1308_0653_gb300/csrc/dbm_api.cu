@@ -340,28 +340,6 @@ int pick_variant(const dbm_params &p)
     return p.precision == DBM_FP64 ? default_variant<double>() : default_variant<float>();
 }
 
-// Theta rows per work item of one simulation.  The persistent CTAs take items
-// blockIdx.x, blockIdx.x + grid, ..., each item loading L + 2 rows (two halo
-// rows), so the busiest CTA handles ceil(items / slots) x (L + 2) rows.  Pick
-// the L that minimises it over the segment counts 1 .. ntheta (L = the
-// smallest rows per segment for that count); the fewest items on ties.
-int pick_rows_per_item(int ntheta, int strips, int slots)
-{
-    int best = ntheta;
-    long long best_cost = -1;
-    for (int segs = 1; segs <= ntheta; ++segs) {
-        const int L = (ntheta + segs - 1) / segs;
-        const long long items = (long long)strips * ((ntheta + L - 1) / L);
-        const long long cost = (items + slots - 1) / slots * (L + 2);
-        if (best_cost < 0 || cost < best_cost) {
-            best = L;
-            best_cost = cost;
-        }
-        if (L == 1) break;
-    }
-    return best;
-}
-
 // Launch shape for a kernel variant: persistent CTAs, one per resident slot,
 // and the rows per item above unless the parameters fix them.
 int configure_launch(dbm_t *h, int variant)
@@ -378,10 +356,10 @@ int configure_launch(dbm_t *h, int variant)
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const dbm_params &p = h->p;
     const int slots = nsm * ki.blocks_per_sm;
-    const int strips = (p.nr + ki.W - 1) / ki.W;
-    int L_rows = p.rows_per_item;
-    if (L_rows == 0) L_rows = pick_rows_per_item(p.ntheta, strips, slots);
-    L_rows = std::min(L_rows, p.ntheta);
+    int32_t L_rows = 0;
+    int64_t n_items = 0;
+    if (dbm_plan_items(p.nr, p.ntheta, ki.W, slots, p.rows_per_item, &L_rows, &n_items) != DBM_OK)
+        return DBM_EINVAL;
     const KernelInfo old_ki = h->ki;
     h->ki = ki;
     if (p.precision == DBM_FP64)
@@ -401,7 +379,7 @@ int configure_launch(dbm_t *h, int variant)
     }
     h->variant = variant;
     h->rows_per_item = L_rows;
-    h->items = strips * ((p.ntheta + L_rows - 1) / L_rows);
+    h->items = (int)n_items;
     h->grid = std::min(h->items, slots);
     // the step arguments carry the launch shape too
     if (p.precision == DBM_FP64)
@@ -541,6 +519,33 @@ size_t dbm_state_bytes(const dbm_params *p)
     int rc = dbm_check(p, nullptr);
     if (rc != DBM_OK && rc != DBM_ECFL) return 0;
     return layout_of(*p).total;
+}
+
+int dbm_plan_items(int32_t nr, int32_t ntheta, int32_t width, int32_t slots, int32_t rows_requested,
+                   int32_t *rows_per_item, int64_t *items)
+{
+    if (nr < 1 || ntheta < 1 || width < 1 || slots < 1 || rows_requested < 0) return DBM_EINVAL;
+    const int64_t strips = ((int64_t)nr + width - 1) / width;
+    int32_t L = ntheta;
+    if (rows_requested > 0) {
+        L = std::min(rows_requested, ntheta);
+    } else {
+        // every segment count per strip, each with its smallest rows per item
+        int64_t best_cost = -1;
+        for (int32_t segs = 1; segs <= ntheta; ++segs) {
+            const int32_t rows = (ntheta + segs - 1) / segs;
+            const int64_t n = strips * ((ntheta + rows - 1) / rows);
+            const int64_t cost = (n + slots - 1) / slots * (rows + 2);
+            if (best_cost < 0 || cost < best_cost) {
+                L = rows;
+                best_cost = cost;
+            }
+            if (rows == 1) break;
+        }
+    }
+    if (rows_per_item) *rows_per_item = L;
+    if (items) *items = strips * ((ntheta + L - 1) / L);
+    return DBM_OK;
 }
 
 int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out)

@@ -70,6 +70,8 @@ def lib():
         L.dbm_check.argtypes = [P, _dp]
         L.dbm_state_bytes.argtypes = [P]
         L.dbm_state_bytes.restype = ctypes.c_size_t
+        L.dbm_plan_items.argtypes = [ctypes.c_int32] * 5 + [ctypes.POINTER(ctypes.c_int32),
+                                                            ctypes.POINTER(ctypes.c_int64)]
         L.dbm_create.argtypes = [P, vp, ctypes.c_size_t, ctypes.POINTER(H)]
         L.dbm_destroy.argtypes = [H]
         L.dbm_init_state.argtypes = [H] + [_dp] * 5 + [vp]
@@ -157,6 +159,14 @@ def dbm_check(p: DbmParams):
 
 def dbm_state_bytes(p: DbmParams) -> int:
     return int(lib().dbm_state_bytes(ctypes.byref(p)))
+
+
+def dbm_plan_items(nr: int, ntheta: int, width: int, slots: int, rows_requested: int = 0):
+    """Host-only work split of one simulation: (rows per item, items per step)."""
+    rows, items = ctypes.c_int32(0), ctypes.c_int64(0)
+    _check(lib().dbm_plan_items(nr, ntheta, width, slots, rows_requested, ctypes.byref(rows),
+                                ctypes.byref(items)), "dbm_plan_items")
+    return rows.value, items.value
 
 
 def dbm_create(p: DbmParams, dev_ptr: int, nbytes: int) -> ctypes.c_void_p:

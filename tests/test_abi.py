@@ -130,3 +130,44 @@ def test_variants_are_numbered_per_precision():
         p.variant = n + 1
         assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL
     assert dbm.dbm_num_variants(7) == 0
+
+
+def _busiest_rows(ntheta, strips, slots, rows):
+    """Rows the busiest persistent CTA loads when items are dealt round-robin,
+    each loading its rows plus two halo rows."""
+    return -(-(strips * -(-ntheta // rows)) // slots) * (rows + 2)
+
+
+@pytest.mark.parametrize("width,slots", [(128, 304), (64, 304), (96, 304), (128, 264)])
+def test_plan_items_minimises_the_busiest_ctas_rows(width, slots):
+    """dbm_plan_items, the split dbm_create uses, against brute force over
+    every rows per item: the busiest CTA loads the fewest rows, and among the
+    best choices the one with the fewest items (least halo traffic) wins."""
+    for nr, nth in [(1, 1), (33, 1), (100, 7), (512, 512), (1536, 1536), (2048, 2048),
+                    (3000, 517), (4096, 4096), (128, 20000)]:
+        rows, items = dbm.dbm_plan_items(nr, nth, width, slots)
+        strips = -(-nr // width)
+        assert 1 <= rows <= nth and items == strips * -(-nth // rows)
+        costs = [_busiest_rows(nth, strips, slots, L) for L in range(1, nth + 1)]
+        best = min(costs)
+        assert _busiest_rows(nth, strips, slots, rows) == best, (nr, nth)
+        assert items == min(strips * -(-nth // L) for L in range(1, nth + 1) if costs[L - 1] == best)
+
+
+def test_plan_items_cases_and_errors():
+    # FP32 2048^2 (W = 128, 2 CTAs on each of 152 SMs): one wave of 304 items
+    assert dbm.dbm_plan_items(2048, 2048, 128, 304) == (108, 304)
+    # FP64 2048^2 (W = 64): 608 items, two per CTA.  The average-load rule
+    # ceil(2048 x 32 / 304) = 216 rows gave 320 items, two for 16 CTAs only,
+    # and twice the rows on the critical path.
+    assert dbm.dbm_plan_items(2048, 2048, 64, 304) == (108, 608)
+    assert (_busiest_rows(2048, 32, 304, 108), _busiest_rows(2048, 32, 304, 216)) == (220, 436)
+    assert dbm.dbm_plan_items(1536, 1536, 64, 304) == (62, 600)
+    # requested rows are kept, capped at ntheta
+    assert dbm.dbm_plan_items(300, 72, 128, 304, 5) == (5, 3 * 15)
+    assert dbm.dbm_plan_items(300, 72, 128, 304, 1000) == (72, 3)
+    for bad in [(0, 8, 128, 304, 0), (8, 0, 128, 304, 0), (8, 8, 0, 304, 0), (8, 8, 128, 0, 0),
+                (8, 8, 128, 304, -1)]:
+        with pytest.raises(dbm.DbmError) as e:
+            dbm.dbm_plan_items(*bad)
+        assert e.value.status == dbm.DBM_EINVAL

@@ -190,6 +190,7 @@ def test_work_items_balance_the_persistent_grid(precision, n):
     strips = -(-n // width)
     L = info["rows_per_item"]
     assert info["items"] == strips * -(-n // L) and info["grid"] == min(info["items"], slots)
+    assert (L, info["items"]) == dbm.dbm_plan_items(n, n, width, slots)
     best = min(_busiest_rows(n, strips, slots, c) for c in range(1, n + 1))
     assert _busiest_rows(n, strips, slots, L) == best
 
