@@ -321,6 +321,21 @@ size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
  * scaled to each simulation: 16 up to 512 theta rows, 32 up to 1024, else 64).
  * Allocates a pinned host staging buffer for the tables.  Synchronous.
  * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
+/* Host-only: the work items of a batched step (what dbm_batch_step launches
+ * after a commit).  Slot s holds an nr[s] x ntheta[s] simulation (nr[s] = 0:
+ * empty), cut into strips of `width` radial sites (the kernel's W) by runs of
+ * rows_per_item[s] theta rows.  The items of all slots are interleaved; when
+ * there are more than `grid` persistent CTAs, they are balanced over the CTAs
+ * longest-processing-time-first with the cost estimate
+ * (rows + 2) (0.3 + 0.7 active lanes / width), and laid out so that CTA c runs
+ * items c, c + grid, c + 2 grid, ..., padded with empty items (slot -1); the
+ * interleaved order is kept if the padded table would exceed max_items.
+ * items (may be NULL): room for max_items quadruples (slot, first radial site,
+ * first theta row, end row).  *n_items receives the count.
+ * Errors: DBM_EINVAL, DBM_ENOMEM (more than max_items items). */
+int dbm_batch_plan(int32_t nslots, const int32_t *nr, const int32_t *ntheta, const int32_t *rows_per_item,
+                   int32_t width, int32_t grid, int64_t max_items, int32_t *items, int64_t *n_items);
+
 int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
                      void *dev_buf, size_t dev_bytes, dbm_batch_t **out);
 

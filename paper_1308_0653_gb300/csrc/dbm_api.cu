@@ -1075,17 +1075,23 @@ void fill_slot(dbm_batch_t *b, int s, unsigned char *dst)
 // padding with empty items (slot -1).  Cost estimate of an item of L rows and
 // a active lanes of W: (L + 2) (0.3 + 0.7 a / W): every row moves through the
 // CTA's pipeline, and the update time grows with the active lanes.  Returns
-// the new item count; keeps the interleaved order if the padded table would
-// exceed max_items.
-long long balance_items(int4 *items, long long n, int grid, int W, const std::vector<dbm_t *> &inst,
-                        long long max_items)
+// the items in launch order; keeps the interleaved order if the padded table
+// would exceed max_items.
+struct PlanItem {
+    int32_t slot, j0, mb, me;  // simulation, first radial site, theta rows [mb, me)
+};
+static_assert(sizeof(PlanItem) == sizeof(int4), "a plan item is one int4 of the device item table");
+
+std::vector<PlanItem> balance_items(const std::vector<PlanItem> &items, int grid, int W, const int32_t *nr,
+                                    long long max_items)
 {
-    if (n <= grid || grid < 1) return n;
+    const long long n = (long long)items.size();
+    if (n <= grid || grid < 1) return items;
     std::vector<double> cost(n);
     for (long long i = 0; i < n; ++i) {
-        const int4 e = items[i];
-        const int active = std::min(W, inst[e.x]->p.nr - e.y);
-        cost[i] = (double)(e.w - e.z + 2) * (0.3 + 0.7 * (double)active / W);
+        const PlanItem &e = items[i];
+        const int active = std::min(W, nr[e.slot] - e.j0);
+        cost[i] = (double)(e.me - e.mb + 2) * (0.3 + 0.7 * (double)active / W);
     }
     std::vector<long long> order(n);
     for (long long i = 0; i < n; ++i) order[i] = i;
@@ -1093,7 +1099,7 @@ long long balance_items(int4 *items, long long n, int grid, int W, const std::ve
     using Load = std::pair<double, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int c = 0; c < grid; ++c) heap.push({0.0, c});
-    std::vector<std::vector<int4>> bins(grid);
+    std::vector<std::vector<PlanItem>> bins(grid);
     for (long long i : order) {
         Load l = heap.top();
         heap.pop();
@@ -1103,11 +1109,12 @@ long long balance_items(int4 *items, long long n, int grid, int W, const std::ve
     size_t K = 0;
     for (const auto &bin : bins) K = std::max(K, bin.size());
     const long long total = (long long)K * grid;
-    if (total > max_items) return n;
+    if (total > max_items) return items;
+    std::vector<PlanItem> out((size_t)total);
     for (size_t k = 0; k < K; ++k)
         for (int c = 0; c < grid; ++c)
-            items[k * grid + c] = k < bins[c].size() ? bins[c][k] : make_int4(-1, 0, 0, 0);
-    return total;
+            out[k * grid + c] = k < bins[c].size() ? bins[c][k] : PlanItem{-1, 0, 0, 0};
+    return out;
 }
 
 int batch_launch(dbm_batch_t *b, int s, cudaStream_t st)
@@ -1179,6 +1186,44 @@ size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision)
 {
     if (max_slots < 1 || max_items < 1 || (precision != DBM_FP32 && precision != DBM_FP64)) return 0;
     return batch_layout(max_slots, max_items, precision).total;
+}
+
+int dbm_batch_plan(int32_t nslots, const int32_t *nr, const int32_t *ntheta, const int32_t *rows_per_item,
+                   int32_t width, int32_t grid, int64_t max_items, int32_t *items, int64_t *n_items)
+{
+    if (nslots < 0 || width < 1 || grid < 1 || max_items < 0 || !n_items ||
+        (nslots > 0 && (!nr || !ntheta || !rows_per_item)))
+        return DBM_EINVAL;
+    *n_items = 0;
+    std::vector<long long> strips(nslots, 0), count(nslots, 0);
+    long long n = 0;
+    for (int s = 0; s < nslots; ++s) {
+        if (nr[s] == 0) continue;  // empty slot
+        if (nr[s] < 0 || ntheta[s] < 1 || rows_per_item[s] < 1) return DBM_EINVAL;
+        strips[s] = (nr[s] + width - 1) / width;
+        count[s] = strips[s] * ((ntheta[s] + rows_per_item[s] - 1) / rows_per_item[s]);
+        n += count[s];
+    }
+    if (n > max_items) return DBM_ENOMEM;
+    // interleave the simulations' items so every CTA gets a share of each
+    std::vector<PlanItem> list;
+    list.reserve((size_t)n);
+    std::vector<long long> cursor(nslots, 0);
+    for (bool more = true; more;) {
+        more = false;
+        for (int s = 0; s < nslots; ++s) {
+            if (cursor[s] >= count[s]) continue;
+            const long long it = cursor[s]++;
+            const int strip = (int)(it % strips[s]), seg = (int)(it / strips[s]);
+            const int mb = seg * rows_per_item[s];
+            list.push_back({s, strip * width, mb, std::min(mb + rows_per_item[s], ntheta[s])});
+            more = true;
+        }
+    }
+    const std::vector<PlanItem> out = balance_items(list, grid, width, nr, max_items);
+    if (items && !out.empty()) std::memcpy(items, out.data(), out.size() * sizeof(PlanItem));
+    *n_items = (int64_t)out.size();
+    return DBM_OK;
 }
 
 int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
@@ -1328,31 +1373,18 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
         else
             fill_slot<float>(b, s, slots + (size_t)s * b->slot_bytes);
     }
-    // interleave the instances' items so every CTA gets a share of each
-    std::vector<long long> cursor(b->max_slots, 0), count(b->max_slots, 0);
+    std::vector<int32_t> nr(b->max_slots, 0), nth(b->max_slots, 0), rows(b->max_slots, 0);
     for (int s = 0; s < b->max_slots; ++s) {
         if (!b->inst[s]) continue;
-        const dbm_params &p = b->inst[s]->p;
-        const int L = batch_rows(b, p);
-        count[s] = (long long)((p.nr + b->ki.W - 1) / b->ki.W) * ((p.ntheta + L - 1) / L);
+        nr[s] = b->inst[s]->p.nr;
+        nth[s] = b->inst[s]->p.ntheta;
+        rows[s] = batch_rows(b, b->inst[s]->p);
     }
-    long long k = 0;
-    bool more = true;
-    while (more) {
-        more = false;
-        for (int s = 0; s < b->max_slots; ++s) {
-            if (cursor[s] >= count[s]) continue;
-            const dbm_params &p = b->inst[s]->p;
-            const int strips = (p.nr + b->ki.W - 1) / b->ki.W;
-            const long long it = cursor[s]++;
-            const int strip = (int)(it % strips), seg = (int)(it / strips);
-            const int L = batch_rows(b, p);
-            const int mb = seg * L;
-            items[k++] = make_int4(s, strip * b->ki.W, mb, std::min(mb + L, p.ntheta));
-            more = true;
-        }
-    }
-    n = balance_items(items, n, b->grid, b->ki.W, b->inst, b->max_items);
+    int64_t planned = 0;
+    const int rc = dbm_batch_plan(b->max_slots, nr.data(), nth.data(), rows.data(), b->ki.W, b->grid,
+                                  b->max_items, reinterpret_cast<int32_t *>(items), &planned);
+    if (rc != DBM_OK) return rc;
+    n = planned;
     b->n_items = (int)n;
     std::memcpy(b->stage + b->off_nitems, &b->n_items, sizeof(int));
     CK(cudaMemcpyAsync(b->buf + b->off_slots, b->stage, (size_t)b->max_slots * b->slot_bytes,

@@ -95,6 +95,9 @@ def lib():
         B = ctypes.c_void_p
         L.dbm_batch_bytes.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int]
         L.dbm_batch_bytes.restype = ctypes.c_size_t
+        _ip = ctypes.POINTER(ctypes.c_int32)
+        L.dbm_batch_plan.argtypes = [ctypes.c_int32, _ip, _ip, _ip, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int64, _ip, ctypes.POINTER(ctypes.c_int64)]
         L.dbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp,
                                        ctypes.c_size_t, ctypes.POINTER(B)]
         L.dbm_batch_destroy.argtypes = [B]
@@ -159,6 +162,21 @@ def dbm_check(p: DbmParams):
 
 def dbm_state_bytes(p: DbmParams) -> int:
     return int(lib().dbm_state_bytes(ctypes.byref(p)))
+
+
+def dbm_batch_plan(nr, ntheta, rows_per_item, width: int, grid: int, max_items: int):
+    """Host-only work items of a batched step: int32 array (n, 4) of (slot,
+    first radial site, first theta row, end row), slot -1 for padding; CTA c
+    runs rows c, c + grid, ...  nr[s] = 0 marks an empty slot."""
+    nr, ntheta, rows = (np.ascontiguousarray(a, dtype=np.int32) for a in (nr, ntheta, rows_per_item))
+    assert nr.shape == ntheta.shape == rows.shape
+    items = np.zeros((max_items, 4), dtype=np.int32)
+    n = ctypes.c_int64(0)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    _check(lib().dbm_batch_plan(len(nr), nr.ctypes.data_as(ip), ntheta.ctypes.data_as(ip),
+                                rows.ctypes.data_as(ip), width, grid, max_items,
+                                items.ctypes.data_as(ip), ctypes.byref(n)), "dbm_batch_plan")
+    return items[:n.value].copy()
 
 
 def dbm_plan_items(nr: int, ntheta: int, width: int, slots: int, rows_requested: int = 0):
