@@ -373,6 +373,13 @@ def params_from(d: dict) -> DbmParams:
 FIELDS = ("rho", "ur", "uth", "T", "lam")
 
 
+def _finish_device(buf):
+    """Wait for all work on the device that holds buf (every stream)."""
+    import torch
+    if buf is not None and buf.is_cuda:
+        torch.cuda.synchronize(buf.device)
+
+
 class Simulation:
     """One simulation on the current CUDA device; device memory is a torch
     uint8 tensor that the library borrows for the handle's lifetime."""
@@ -440,6 +447,10 @@ class Simulation:
 
     def close(self):
         if self.h is not None:
+            # steps may still be queued on any stream the caller passed, and
+            # once the buffer is dropped torch may hand it to another tensor:
+            # finish the device's work first (dbm_destroy does not wait)
+            _finish_device(self.buf)
             dbm_destroy(self.h)
             self.h = None
             self.buf = None
@@ -494,6 +505,7 @@ class Batch:
 
     def close(self):
         if self.b is not None:
+            _finish_device(self.buf)  # queued batched steps read the tables in buf
             dbm_batch_destroy(self.b)
             self.b = None
             self.buf = None
