@@ -325,7 +325,7 @@ size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
  * after a commit).  Slot s holds an nr[s] x ntheta[s] simulation (nr[s] = 0:
  * empty), cut into strips of `width` radial sites (the kernel's W) by runs of
  * rows_per_item[s] theta rows.  The items of all slots are interleaved; when
- * there are more than `grid` persistent CTAs, they are balanced over the CTAs
+ * they outnumber the `grid` persistent CTAs, they are balanced over the CTAs
  * longest-processing-time-first with the cost estimate
  * (rows + 2) (0.3 + 0.7 active lanes / width), and laid out so that CTA c runs
  * items c, c + grid, c + 2 grid, ..., padded with empty items (slot -1); the
