@@ -271,3 +271,59 @@ def test_totals_are_area_weighted(orc):
     t = orc.totals(p, f)
     np.testing.assert_allclose(t, [1.3 * area, 1.3 * 0.4 * area, -1.3 * 0.2 * area,
                                    1.3 * (1.1 + 0.5 * (0.16 + 0.04)) * area], rtol=1e-13)
+
+
+def _conserved(orc, p, f, lam):
+    """Mass, momentum (polar components at each site's own theta) and total
+    energy rho (T + u^2 / 2) densities (D = 2), per site."""
+    m = orc.macro(p, f, lam)
+    rho = m["rho"]
+    return {"mass": rho, "mom_r": rho * m["ur"], "mom_th": rho * m["uth"],
+            "energy": rho * (m["T"] + 0.5 * (m["ur"] ** 2 + m["uth"] ** 2))}, m
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_collision_conserves_mass_momentum_and_energy(orc, seed):
+    """Sec. II.B-II.C: f^eq is built from the moments of f, so BGK relaxation
+    keeps mass, momentum and energy at every site.  A spatially uniform f far
+    from equilibrium (each velocity scaled by its own random factor, which
+    changes all its moments) has no streaming differences: one step is the
+    collision alone, and it moves f a long way while the conserved densities
+    stay to round-off."""
+    w = W.uniform_state(6, 16, 1.1, 0.25, -0.15, 1.4, 0.0, dt=1e-4, tau=3e-4)
+    p = _p(orc, w)
+    f, lam = orc.init(p, w.fields)
+    rng = np.random.default_rng(100 + seed)
+    f = f * (1.0 + rng.uniform(-0.3, 0.3, 33))[:, None, None]
+    before, _ = _conserved(orc, p, f, lam)
+    fn, lam_n, _ = orc.step(p, f, lam)
+    after, _ = _conserved(orc, p, fn, lam_n)
+    assert np.abs(fn - f).max() > 1e-3          # relaxed by far more than round-off
+    for k in before:
+        np.testing.assert_allclose(after[k], before[k], rtol=0, atol=2e-14, err_msg=k)
+
+
+@pytest.mark.parametrize("mode", ["explicit", "consistent"])
+def test_reaction_adds_exactly_the_heat_release(orc, mode):
+    """Sec. II.A and III.A: the chemical term has no mass or momentum moment and
+    an energy moment rho Q R.  One step of a uniform burning gas (T > T_th)
+    keeps mass and momentum and adds dt rho Q R to the energy density, with
+    R = (1 - lambda)(a + b lambda), a = omega1 P^m, b = omega2 P^n, P = rho T
+    at time t (the printed equations); with the consistent reading
+    R = (Lambda(lambda) - lambda) / dt the energy gained is exactly rho Q times
+    the step's change of lambda."""
+    rho, T, lam0, Q, w1, w2 = 1.1, 1.4, 0.3, 1.7, 2.0, 3.0
+    w = W.uniform_state(6, 16, rho, 0.25, -0.15, T, lam0, dt=1e-4, tau=3e-4, omega1=w1,
+                        omega2=w2, Q=Q)
+    p = _p(orc, w, reaction_energy=mode)
+    f, lam = orc.init(p, w.fields)
+    before, _ = _conserved(orc, p, f, lam)
+    fn, lam_n, _ = orc.step(p, f, lam)
+    after, m = _conserved(orc, p, fn, lam_n)
+    for k in ("mass", "mom_r", "mom_th"):
+        np.testing.assert_allclose(after[k], before[k], rtol=0, atol=2e-14, err_msg=k)
+    P = rho * T
+    R = (1.0 - lam0) * (w1 * P + w2 * P * lam0)
+    gain = rho * Q * (R * 1e-4 if mode == "explicit" else m["lam"] - lam0)
+    assert np.all(m["lam"] > lam0)
+    np.testing.assert_allclose(after["energy"] - before["energy"], gain, rtol=1e-10, atol=0)
