@@ -125,11 +125,27 @@ def _check(status: int, where: str):
         raise DbmError(status, where)
 
 
-def _ptr(a):
+def _ptr(a, size=None):
+    """double* of a C-contiguous float64 array (None passes through); with
+    `size`, the array must hold exactly that many elements, since the library
+    reads or writes that many."""
     if a is None:
         return None
-    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    if size is not None and a.size != size:
+        raise ValueError(f"array of {a.size} elements where {size} are needed")
     return a.ctypes.data_as(_dp)
+
+
+def _field_arrays(fields, n: int):
+    """The five host fields (rho, u_r, u_theta, T, lambda) as contiguous
+    float64 arrays of n = ntheta x nr elements each (copies only if needed)."""
+    arrs = [np.ascontiguousarray(fields[k], dtype=np.float64) for k in FIELDS]
+    for k, a in zip(FIELDS, arrs):
+        if a.size != n:
+            raise ValueError(f"field {k}: {a.size} values for a grid of {n} sites")
+    return arrs
 
 
 def _stream(stream):
@@ -169,7 +185,8 @@ def dbm_batch_plan(nr, ntheta, rows_per_item, width: int, grid: int, max_items: 
     first radial site, first theta row, end row), slot -1 for padding; CTA c
     runs rows c, c + grid, ...  nr[s] = 0 marks an empty slot."""
     nr, ntheta, rows = (np.ascontiguousarray(a, dtype=np.int32) for a in (nr, ntheta, rows_per_item))
-    assert nr.shape == ntheta.shape == rows.shape
+    if not nr.shape == ntheta.shape == rows.shape or nr.ndim != 1:
+        raise ValueError("nr, ntheta and rows_per_item must be 1-D arrays of one length")
     items = np.zeros((max_items, 4), dtype=np.int32)
     n = ctypes.c_int64(0)
     ip = ctypes.POINTER(ctypes.c_int32)
@@ -199,7 +216,11 @@ def dbm_destroy(h):
 
 
 def dbm_init_state(h, rho, ur, uth, T, lam, stream=None):
+    """Host fields of the handle's grid (their sizes are the caller's to get
+    right here; Simulation.init_state checks them against the grid)."""
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (rho, ur, uth, T, lam)]
+    if len({a.size for a in arrs}) != 1:
+        raise ValueError("the five fields differ in size")
     _check(lib().dbm_init_state(h, *[_ptr(a) for a in arrs], _stream(stream)), "dbm_init_state")
 
 
@@ -214,7 +235,7 @@ def dbm_step(h, nsteps: int, stream=None):
 
 def dbm_moments(h, rho=None, ur=None, uth=None, T=None, lam=None, totals=None, stream=None,
                 raise_nonfinite=True):
-    st = lib().dbm_moments(h, _ptr(rho), _ptr(ur), _ptr(uth), _ptr(T), _ptr(lam), _ptr(totals),
+    st = lib().dbm_moments(h, _ptr(rho), _ptr(ur), _ptr(uth), _ptr(T), _ptr(lam), _ptr(totals, 4),
                            _stream(stream))
     if st == DBM_ENONFINITE and not raise_nonfinite:
         return st
@@ -401,7 +422,7 @@ class Simulation:
         return (self.p.ntheta, self.p.nr)
 
     def init_state(self, fields: dict, stream=None):
-        dbm_init_state(self.h, *[fields[k] for k in FIELDS], stream=stream)
+        dbm_init_state(self.h, *_field_arrays(fields, self.p.nr * self.p.ntheta), stream=stream)
 
     def step(self, nsteps: int, stream=None):
         dbm_step(self.h, nsteps, stream)
@@ -443,6 +464,9 @@ class Simulation:
         dt = np.float64 if self.p.precision == DBM_FP64 else np.float32
         f = np.ascontiguousarray(f, dtype=dt)
         lam = np.ascontiguousarray(lam, dtype=dt)
+        n = self.p.nr * self.p.ntheta
+        if f.size != NV * n or lam.size != n:
+            raise ValueError(f"state of {f.size} + {lam.size} values for {NV} x {n} + {n}")
         dbm_import_state(self.h, f, lam, steps, stream)
 
     def close(self):
@@ -577,8 +601,8 @@ def dbm_server_create(cfg: DbmServerConfig, dev_ptr: int, nbytes: int):
 
 
 def dbm_submit(s, params: DbmParams, fields: dict, nsteps: int) -> int:
-    arrs = {k: np.ascontiguousarray(fields[k], dtype=np.float64) for k in FIELDS}
-    f = DbmFields(*[_ptr(arrs[k]) for k in FIELDS])
+    arrs = _field_arrays(fields, int(params.nr) * int(params.ntheta))
+    f = DbmFields(*[_ptr(a) for a in arrs])
     t = ctypes.c_uint64(0)
     _check(_server_lib().dbm_submit(s, ctypes.byref(params), ctypes.byref(f), int(nsteps),
                                     ctypes.byref(t)), "dbm_submit")

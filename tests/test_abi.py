@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1308_0653_gb300 import dbm
@@ -171,3 +172,27 @@ def test_plan_items_cases_and_errors():
         with pytest.raises(dbm.DbmError) as e:
             dbm.dbm_plan_items(*bad)
         assert e.value.status == dbm.DBM_EINVAL
+
+
+def test_binding_checks_host_arrays_before_the_library_reads_them():
+    """Host arrays reach the library as bare pointers, so the binding checks
+    type, layout and size first (exceptions, not asserts)."""
+    n = 12 * 7
+    good = {k: np.zeros((12, 7)) for k in dbm.FIELDS}
+    arrs = dbm._field_arrays(good, n)
+    assert [a.size for a in arrs] == [n] * 5 and all(a.flags["C_CONTIGUOUS"] for a in arrs)
+    ints = dict(good, T=np.ones((12, 7), dtype=np.int64))   # converted, not rejected
+    assert dbm._field_arrays(ints, n)[3].dtype == np.float64
+    with pytest.raises(ValueError):
+        dbm._field_arrays(dict(good, lam=np.zeros((12, 6))), n)
+    with pytest.raises(KeyError):
+        dbm._field_arrays({k: v for k, v in good.items() if k != "uth"}, n)
+    assert dbm._ptr(None) is None and dbm._ptr(np.zeros(4), 4) is not None
+    with pytest.raises(ValueError):
+        dbm._ptr(np.zeros(3), 4)
+    with pytest.raises(TypeError):
+        dbm._ptr(np.zeros(4, dtype=np.float32))
+    with pytest.raises(TypeError):
+        dbm._ptr(np.zeros((4, 4))[:, 1])                     # not contiguous
+    with pytest.raises(ValueError):
+        dbm.dbm_batch_plan([5, 6], [5], [1, 1], 128, 8, 100)
