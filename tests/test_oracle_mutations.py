@@ -72,6 +72,22 @@ MUTANTS = [
     ("M*_{3,1} component", "out[7] += 0.5 * gq * s2 * a;", "out[7] += 0.5 * gq * s2 * b;"),
     ("M*_{4,2} factor", "out[9] += 0.5 * gq * s2 * a * a;", "out[9] += gq * s2 * a * a;"),
     ("M*_3 index", "out[5] += gq * a * b * b;", "out[5] += gq * a * a * b;"),
+    ("upwind side swapped (theta)", "if (Ct >= 0.0)\n                    ft_star",
+     "if (Ct < 0.0)\n                    ft_star"),
+    ("lambda upwind side swapped (r)", "if (ur >= 0.0)\n                lr_star",
+     "if (ur < 0.0)\n                lr_star"),
+    ("lambda upwind side swapped (theta)", "if (uth >= 0.0)\n                lt_star",
+     "if (uth < 0.0)\n                lt_star"),
+    ("rate b uses exponent m", "bb = p->omega2 * pow(P, p->n);", "bb = p->omega2 * pow(P, p->m);"),
+    ("rate b term without (1 - lambda)", "bb * lam * (1.0 - lam)", "bb * lam"),
+    ("lambda step numerator sign", "- a * (1.0 - lam)) / ((a + b * lam) * E",
+     "+ a * (1.0 - lam)) / ((a + b * lam) * E"),
+    ("lambda step E without b", "double E = exp((a + b) * dt);", "double E = exp(a * dt);"),
+    ("totals area without r", "double w = r_of(p, j) * dr * dth;", "double w = dr * dth;"),
+    ("totals p_y sign of u_theta", "py += rho * (ur * sin(th) + uth * cos(th)) * w;",
+     "py += rho * (ur * sin(th) - uth * cos(th)) * w;"),
+    ("totals energy without kinetic part", "en += (rho * T + 0.5 * rho * (ur * ur + uth * uth)) * w;",
+     "en += (rho * T) * w;"),
 ]
 
 PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",

@@ -173,6 +173,35 @@ def test_lambda_is_carried_upwind_by_the_flow(orc):
     assert lam.min() >= 0.0 and lam.max() <= 1.0
 
 
+def test_lambda_is_carried_upwind_in_theta(orc):
+    """Eq. (Eqlambda) transport part in theta: on a thin annulus far from the
+    axis (r = 100, locally a plane), a lambda front in a uniform azimuthal
+    flow u_theta (no reaction) moves along theta by u_theta t of arc length,
+    to first order, for either sign of u_theta."""
+    nr, nth, r_in, r_out = 4, 2000, 100.0, 100.4
+    r, th = W.grid(nr, nth, r_in, r_out)
+    ds = r[0, 1] * (th[1, 0] - th[0, 0])               # arc length of a row at column 1
+    dt = 0.4 * min((r_out - r_in) / nr, r_in * 2 * math.pi / nth) / 12.5
+    for u in (0.5, -0.5):
+        w = W.uniform_state(nr, nth, 1.0, 0.0, 0.0, 1.0, 0.0, r_in=r_in, r_out=r_out)
+        w.fields["ur"] = np.zeros((nth, nr))
+        w.fields["uth"] = np.full((nth, nr), u)
+        w.fields["lam"] = np.ascontiguousarray(np.where(th < math.pi, 1.0, 0.0))
+        n = int(round(5 * ds / abs(u) / dt))              # about five rows
+        p = _p(orc, w, dt=dt, tau=1e-3)
+        f, lam = orc.init(p, w.fields)
+        for _ in range(n):
+            f, lam, _ = orc.step(p, f, lam)
+        prof = lam[:, 1]
+        # the lambda = 1/2 crossing near theta = pi (rows 900 .. 1100)
+        seg = prof[900:1100]
+        k = 900 + np.nonzero(seg < 0.5)[0][0]
+        x = (k - 1) + (0.5 - prof[k - 1]) / (prof[k] - prof[k - 1])
+        moved = (x - (nth // 2 - 0.5)) * ds
+        assert moved == pytest.approx(u * n * dt, abs=1.5 * ds), u
+        assert lam.min() >= 0.0 and lam.max() <= 1.0
+
+
 def test_outflow_boundary_lets_a_uniform_flow_through(orc):
     """Zero-gradient radial ghosts: a uniform radial-free flow (Cartesian
     uniform velocity) stays uniform at both radial boundaries."""
@@ -263,11 +292,13 @@ def test_totals_are_area_weighted(orc):
     """Totals integrate with the area element r dr dtheta at cell centres
     (exact for fields linear in r): a uniform state has mass rho pi (r_out^2 -
     r_in^2), momentum rho pi (r_out^2 - r_in^2) (ux, uy) and energy
-    rho (T + u^2/2) times the area."""
-    w = W.uniform_state(7, 24, 1.3, 0.4, -0.2, 1.1, 0.0, r_in=0.3, r_out=1.7)
+    rho (T + u^2/2) times the area.  The annulus' mean radius is 1.2, not 1,
+    so an area element without r would give a different total."""
+    w = W.uniform_state(7, 24, 1.3, 0.4, -0.2, 1.1, 0.0, r_in=0.3, r_out=2.1)
     p = _p(orc, w)
     f, lam = orc.init(p, w.fields)
-    area = math.pi * (1.7 ** 2 - 0.3 ** 2)
+    area = math.pi * (2.1 ** 2 - 0.3 ** 2)
+    assert abs(area - 2 * math.pi * (2.1 - 0.3)) > 0.1 * area
     t = orc.totals(p, f)
     np.testing.assert_allclose(t, [1.3 * area, 1.3 * 0.4 * area, -1.3 * 0.2 * area,
                                    1.3 * (1.1 + 0.5 * (0.16 + 0.04)) * area], rtol=1e-13)
