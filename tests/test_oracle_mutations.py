@@ -88,6 +88,21 @@ MUTANTS = [
      "py += rho * (ur * sin(th) - uth * cos(th)) * w;"),
     ("totals energy without kinetic part", "en += (rho * T + 0.5 * rho * (ur * ur + uth * uth)) * w;",
      "en += (rho * T) * w;"),
+    ("f^eq quadratic term factor", "double term2 = vu * vu / (2.0 * T * T) * (1.0 - u2 / (2.0 * T));",
+     "double term2 = vu * vu / (2.0 * T * T) * (1.0 - u2 / (4.0 * T));"),
+    ("f^eq zeroth term u^2 sign", "double term0 = 1.0 - u2 / (2.0 * T)", "double term0 = 1.0 + u2 / (2.0 * T)"),
+    ("f^eq rest weight index", "feq[q] = rho * F[k] *", "feq[q] = rho * F[k == 0 ? 1 : k] *"),
+    ("moments: u_r from theta momentum", "double u_r = jr / r, u_t = jt / r;",
+     "double u_r = jt / r, u_t = jt / r;"),
+    ("moments: T about the origin", "double dr_ = vr[q] - u_r, dt_ = vth[q] - u_t;\n        e +=",
+     "double dr_ = vr[q], dt_ = vth[q];\n        e +="),
+    ("M: (v - u)^2 without u", "double dr_ = vr[q] - ur, dt_ = vth[q] - uth;\n        double c2",
+     "double dr_ = vr[q], dt_ = vth[q];\n        double c2"),
+    ("ignition gate not strict", "if (T > p->T_th) {", "if (T >= p->T_th) {"),
+    ("consistent R without 1/dt", "R = (lam_react - lam[s]) / dt;", "R = (lam_react - lam[s]);"),
+    ("init: lambda not copied", "lam_f[s] = lam[s];", "lam_f[s] = 0.0;"),
+    ("inner ghost reflects", "return f[at(p, N, q, m, 0)];\n}", "return f[at(p, N, q, m, 1)];\n}"),
+    ("ring speed index", "vr[vindex(k, i)] = v[k - 1] * cos(ang);", "vr[vindex(k, i)] = v[k % 4] * cos(ang);"),
 ]
 
 PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",
