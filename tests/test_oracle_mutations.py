@@ -1,6 +1,7 @@
 """Mutation check of the oracle's pins: plant one plausible mistake at a time
 (a dropped term, a wrong sign, factor or index) in a temporary copy of the
-oracle source, rebuild it, and require the pin suite to fail.
+oracle source (the C oracle, or the ZND solver), rebuild it, and require the
+pin suite to fail.
 
 Only the temporary copy is changed; the oracle in the tree is untouched.
 """
@@ -105,15 +106,25 @@ MUTANTS = [
     ("ring speed index", "vr[vindex(k, i)] = v[k - 1] * cos(ang);", "vr[vindex(k, i)] = v[k % 4] * cos(ang);"),
 ]
 
+ZND_MUTANTS = [
+    ("omega1 term uses n", "omega1 * P ** m", "omega1 * P ** n"),
+    ("omega2 term without lambda", "omega2 * P ** n * lm)", "omega2 * P ** n)"),
+    ("left-point rule", "lm = 0.5 * (lam[i - 1] + lam[i])", "lm = lam[i - 1]"),
+    ("larger Hugoniot root", "v = (b - math.sqrt(", "v = (b + math.sqrt("),
+    ("enthalpy factor", "g = gamma / (gamma - 1.0)", "g = gamma / (gamma + 1.0)"),
+    ("CJ bisection keeps the wrong half", "            hi = mid\n        else:\n            lo = mid",
+     "            lo = mid\n        else:\n            hi = mid"),
+]
+
 PIN_FILES = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_reaction.py",
              "tests/test_oracle_step.py", "tests/test_oracle_noneq.py", "tests/test_oracle_sector.py",
              "tests/test_oracle_cj.py"]
 
 
-def _run_pins(name, old, new):
-    """Run the pin suite on a copy of the oracle with `old` replaced by `new`;
-    returns pytest's summary line."""
-    src = open(os.path.join(ROOT, "oracle", "dbm_oracle.c")).read()
+def _run_pins(name, old, new, source="dbm_oracle.c", pins=PIN_FILES):
+    """Run the pin suite on a copy of the oracle with `old` replaced by `new`
+    in oracle/<source>; returns pytest's summary line."""
+    src = open(os.path.join(ROOT, "oracle", source)).read()
     assert src.count(old) >= 1, f"mutation pattern not found: {name}"
     tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
     try:
@@ -125,11 +136,11 @@ def _run_pins(name, old, new):
         for fn in ("__init__.py", "workloads.py"):
             shutil.copy(os.path.join(ROOT, "paper_1308_0653_gb300", fn),
                         os.path.join(tmp, "paper_1308_0653_gb300", fn))
-        with open(os.path.join(tmp, "oracle", "dbm_oracle.c"), "w") as fh:
+        with open(os.path.join(tmp, "oracle", source), "w") as fh:
             fh.write(src.replace(old, new, 1))
         env = dict(os.environ, ORACLE_THREADS="2")
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            *PIN_FILES], cwd=tmp, capture_output=True, text=True, timeout=900,
+                            *pins], cwd=tmp, capture_output=True, text=True, timeout=900,
                            env=env)
         lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
         return lines[-1] if lines else r.stderr[-200:]
@@ -145,5 +156,14 @@ def test_every_planted_mistake_fails_a_pin():
     with cf.ThreadPoolExecutor(workers) as ex:
         res = dict(zip([m[0] for m in MUTANTS], ex.map(lambda m: _run_pins(*m), MUTANTS)))
     # caught = a pin assertion failed (a build or collection error does not count)
+    survivors = {k: v for k, v in res.items() if "failed" not in v}
+    assert not survivors, f"mutations not caught by any pin: {survivors}"
+
+
+def test_every_planted_znd_mistake_fails_a_pin():
+    pins = ["tests/test_oracle_znd.py"]
+    control = _run_pins("control", "import math", "import math", "znd.py", pins)
+    assert "passed" in control and "failed" not in control and "error" not in control, control
+    res = {m[0]: _run_pins(*m, "znd.py", pins) for m in ZND_MUTANTS}
     survivors = {k: v for k, v in res.items() if "failed" not in v}
     assert not survivors, f"mutations not caught by any pin: {survivors}"

@@ -62,6 +62,24 @@ def test_zone_length_without_heat_release_is_logarithmic():
     np.testing.assert_allclose(z["x"][1:], exact[1:], rtol=1e-6)
 
 
+def test_zone_length_with_both_rate_terms_has_its_closed_form():
+    """Q = 0 keeps the shocked state uniform, so with a = omega1 P1^m and
+    b = omega2 P1^n the rate is (1 - lam)(a + b lam) and, by partial
+    fractions, x(lam) = w1 / (a + b) ln[(a + b lam) / (a (1 - lam))].  The
+    exponents differ (m = 1, n = 2) and P1 = 5.67 is far from 1, so each
+    term must carry its own exponent and the second its factor lam.  (b / a
+    is kept near 1.6: the integral is a midpoint rule, and a steeper rate
+    near lam = 0 would show its second-order error above 1e-6.)"""
+    D, om1, om2, m, n = 3.0, 7.0, 2.0, 1.0, 2.0
+    z = znd.profile(D=D, Q=0.0, omega1=om1, omega2=om2, m=m, n=n, lam_max=1 - 1e-5)
+    rho1, P1, _, u1 = znd.state(0.0, D, Q=0.0)
+    assert P1 == pytest.approx(1.0 + 4.0 / 3.0 * (D * D / 2.0 - 1.0), rel=1e-12)
+    a, b = om1 * P1 ** m, om2 * P1 ** n
+    lam = z["lam"][1:]
+    exact = (D - u1) / (a + b) * np.log((a + b * lam) / (a * (1.0 - lam)))
+    np.testing.assert_allclose(z["x"][1:], exact, rtol=1e-6)
+
+
 def test_below_cj_speed_there_is_no_steady_wave():
     with pytest.raises(ValueError):
         znd.state(1.0, 0.99 * znd.cj_speed())
