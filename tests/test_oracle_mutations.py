@@ -104,6 +104,17 @@ MUTANTS = [
     ("init: lambda not copied", "lam_f[s] = lam[s];", "lam_f[s] = 0.0;"),
     ("inner ghost reflects", "return f[at(p, N, q, m, 0)];\n}", "return f[at(p, N, q, m, 1)];\n}"),
     ("ring speed index", "vr[vindex(k, i)] = v[k - 1] * cos(ang);", "vr[vindex(k, i)] = v[k % 4] * cos(ang);"),
+    ("noneq: v* about the origin", "double a = vr[q] - ur, b = vth[q] - uth;  /* v* in polar components */",
+     "double a = vr[q], b = vth[q];  /* v* in polar components */"),
+    ("noneq: M*_2 r-theta component", "out[1] += gq * a * b;", "out[1] += gq * a * a;"),
+    ("noneq: M*_3 rrr factor", "out[3] += gq * a * a * a;", "out[3] += gq * a * a * a * 0.5;"),
+    ("noneq: M*_{3,1} theta", "out[8] += 0.5 * gq * s2 * b;", "out[8] += 0.5 * gq * s2 * a;"),
+    ("noneq: M*_{4,2} theta-theta", "out[11] += 0.5 * gq * s2 * b * b;", "out[11] += 0.5 * gq * s2 * a * b;"),
+    ("noneq: equilibrium part from f", "central_with_velocities(vr, vth, feq, 1, ur, uth, me);",
+     "central_with_velocities(vr, vth, f + s, N, ur, uth, me);"),
+    ("noneq: sign", "out[c * N + s] = mf[c] - me[c];", "out[c * N + s] = me[c] - mf[c];"),
+    ("run: f buffers not swapped", "double *tf = fa; fa = fb; fb = tf;", "/* no swap */"),
+    ("run: lambda buffers not swapped", "double *tl = la; la = lb; lb = tl;", "/* no swap */"),
 ]
 
 ZND_MUTANTS = [

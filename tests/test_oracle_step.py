@@ -358,3 +358,20 @@ def test_reaction_adds_exactly_the_heat_release(orc, mode):
     gain = rho * Q * (R * 1e-4 if mode == "explicit" else m["lam"] - lam0)
     assert np.all(m["lam"] > lam0)
     np.testing.assert_allclose(after["energy"] - before["energy"], gain, rtol=1e-10, atol=0)
+
+
+def test_run_equals_repeated_steps(orc):
+    """oracle.run (init, n steps and the moments in one call: the driver the
+    GPU parity tests compare with) gives bit for bit what init, n separate
+    steps and macro give, on a state where every term is active."""
+    w = W.random_smooth(24, 16, seed=5, amp=0.15, dt=2e-4, omega1=2.0, omega2=3.0)
+    p = _p(orc, w)
+    n = 7
+    out = orc.run(p, w.fields, n)
+    f, lam = orc.init(p, w.fields)
+    for _ in range(n):
+        f, lam, _ = orc.step(p, f, lam)
+    ref = orc.macro(p, f, lam)
+    for k in ("rho", "ur", "uth", "T", "lam"):
+        assert np.array_equal(out[k], ref[k]), k
+    assert not np.array_equal(ref["rho"], w.fields["rho"])
