@@ -115,6 +115,20 @@ MUTANTS = [
     ("noneq: sign", "out[c * N + s] = mf[c] - me[c];", "out[c * N + s] = me[c] - mf[c];"),
     ("run: f buffers not swapped", "double *tf = fa; fa = fb; fb = tf;", "/* no swap */"),
     ("run: lambda buffers not swapped", "double *tl = la; la = lb; lb = tl;", "/* no swap */"),
+    ("sector wrap above rotates the wrong way", "return f[at(p, N, p->sector ? vrot(q, -1) : q, 0, j)];",
+     "return f[at(p, N, p->sector ? vrot(q, 1) : q, 0, j)];"),
+    ("theta wrap above to the last row", "return f[at(p, N, p->sector ? vrot(q, -1) : q, 0, j)];",
+     "return f[at(p, N, p->sector ? vrot(q, -1) : q, p->ntheta - 1, j)];"),
+    ("lambda centre mirror missing",
+     "if (p->r_bc_inner == 1 && !p->sector) return lam[(long)((m + p->ntheta / 2) % p->ntheta) * p->nr];",
+     "if (p->r_bc_inner == 1 && !p->sector) return lam[(long)m * p->nr];"),
+    ("lambda outer ghost reflects", "return lam[(long)m * p->nr + (j < p->nr - 1 ? j + 1 : p->nr - 1)];",
+     "return lam[(long)m * p->nr + (j < p->nr - 1 ? j + 1 : p->nr - 2)];"),
+    ("lambda inner ghost reflects", "    return lam[(long)m * p->nr];\n}", "    return lam[(long)m * p->nr + 1];\n}"),
+    ("lambda theta wrap below", "return lam[(long)(m > 0 ? m - 1 : p->ntheta - 1) * p->nr + j];",
+     "return lam[(long)(m > 0 ? m - 1 : 0) * p->nr + j];"),
+    ("lambda theta wrap above", "return lam[(long)(m < p->ntheta - 1 ? m + 1 : 0) * p->nr + j];",
+     "return lam[(long)(m < p->ntheta - 1 ? m + 1 : p->ntheta - 1) * p->nr + j];"),
 ]
 
 ZND_MUTANTS = [

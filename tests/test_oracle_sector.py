@@ -79,3 +79,30 @@ def test_centre_rule_reverses_the_radial_velocity(orc):
     mc, _ = _run(orc, w.fields, nr, s, 0.0, 1.0, 1, 1, 200, dt)
     assert mc["rho"][0, 0] > 1.05
     assert abs(mc["ur"][0, 0]) < 0.3
+
+
+def test_lambda_front_crosses_the_centre_of_a_full_disc(orc):
+    """Full 2 pi disc with the centre rule: the inner ghost of a lambda cell
+    is the cell across the centre (row m + ntheta / 2, same radius).  In a
+    uniform Cartesian flow u_x (uniform f, an exact steady state of the
+    update) a lambda front x = x0 moves at u_x straight through the centre:
+    once it has passed, the innermost cells downstream are burnt and the
+    front on the +x axis (row 0) has moved u_x t."""
+    nr, nth, ux, x0, t_end = 32, 32, 0.5, -0.25, 0.8
+    w = W.uniform_state(nr, nth, 1.0, ux, 0.0, 1.0, 0.0, r_in=0.0, r_out=1.0)
+    r, th = W.grid(nr, nth, 0.0, 1.0)
+    w.fields["lam"] = np.ascontiguousarray(np.where(r * np.cos(th) < x0, 1.0, 0.0))
+    dt = 0.4 * (0.5 / nr) * (2 * math.pi / nth) / 12.5     # innermost ring's arc
+    n = int(round(t_end / dt))
+    p = orc.make_params(nr=nr, ntheta=nth, r_in=0.0, r_out=1.0, dt=dt, tau=1e-3,
+                        omega1=0.0, omega2=0.0, r_bc_inner=1)
+    f, lam = orc.init(p, w.fields)
+    for _ in range(n):
+        f, lam, _ = orc.step(p, f, lam)
+    m = orc.macro(p, f, lam)
+    np.testing.assert_allclose(m["rho"], 1.0, atol=1e-12)            # the flow stays uniform
+    prof = lam[0]                                                     # theta = 0: the +x axis
+    assert prof[0] > 0.75
+    k = np.nonzero(prof < 0.5)[0][0]
+    xf = r[0, k - 1] + (0.5 - prof[k - 1]) / (prof[k] - prof[k - 1]) * (r[0, k] - r[0, k - 1])
+    assert xf == pytest.approx(x0 + ux * n * dt, abs=2.0 / nr)

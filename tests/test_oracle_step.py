@@ -288,6 +288,28 @@ def test_radial_ghosts_are_zero_gradient(orc):
                 assert abs(change[-1]) < 1e-15 and change[0] == pytest.approx(-Cr * b * dr, abs=1e-15)
 
 
+@pytest.mark.parametrize("u", [-0.5, 0.5])
+def test_lambda_radial_ghosts_are_zero_gradient(orc, u):
+    """The radial ghosts of lambda copy the boundary cell (as for f): in a
+    uniform radial flow u_r with lambda linear in r, the cell whose upwind
+    side is the ghost keeps its lambda, and every other cell gains
+    -u_r dt times the gradient."""
+    nr, nth, b = 10, 8, 0.05
+    w = W.uniform_state(nr, nth, 1.0, 0.0, 0.0, 1.0, 0.0, r_in=10.0, r_out=11.0)
+    r, _ = W.grid(nr, nth, 10.0, 11.0)
+    w.fields["ur"] = np.full((nth, nr), u)
+    w.fields["uth"] = np.zeros((nth, nr))
+    w.fields["lam"] = np.ascontiguousarray(0.3 + b * (r - 10.0))
+    dt = 0.4 * (1.0 / nr) / 12.5
+    p = _p(orc, w, dt=dt, tau=1e-3)
+    f, lam = orc.init(p, w.fields)
+    _, lam_n, _ = orc.step(p, f, lam)
+    change = lam_n - lam
+    edge, inner = (slice(-1, None), slice(None, -1)) if u < 0 else (slice(0, 1), slice(1, None))
+    np.testing.assert_allclose(change[:, edge], 0.0, atol=1e-16)
+    np.testing.assert_allclose(change[:, inner], -u * dt * b, rtol=1e-9)
+
+
 def test_totals_are_area_weighted(orc):
     """Totals integrate with the area element r dr dtheta at cell centres
     (exact for fields linear in r): a uniform state has mass rho pi (r_out^2 -
