@@ -89,3 +89,32 @@ def test_serving_requests_span_the_stated_ranges():
     assert {w.params["omega1"] for w in ws} == {1.0, 2.0, 4.0}
     kinds = ["explosion" in w.name for w in ws]
     assert 0.25 < np.mean(kinds) < 0.75
+
+
+def test_paper_disc_runs_use_the_printed_shock_state():
+    """Sec. III.C-D: the implosion ring and the explosion driver are the
+    printed state (rho, T, |u_r|) = (1.5, 1.55556, 0.666667) into gas at rest
+    (1, 1, 0), which for gamma = 2 (P = rho T, c0 = sqrt 2) is the normal
+    shock of speed 2, Mach^2 = 2: rho1 = (g+1) M^2 / ((g-1) M^2 + 2) = 3/2,
+    P1 = 1 + 2g (M^2 - 1) / (g+1) = 7/3, u1 = D (1 - 1/rho1) = 2/3."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_numbers.json")))["implosion_shock_state"]
+    g, D = 2.0, 2.0
+    M2 = D * D / g
+    rho1 = (g + 1) * M2 / ((g - 1) * M2 + 2)
+    P1 = 1 + 2 * g * (M2 - 1) / (g + 1)
+    u1 = D * (1 - 1 / rho1)
+    assert (gold["rho"], gold["T"], -gold["u_r"]) == pytest.approx((rho1, P1 / rho1, u1), abs=1e-5)
+    imp = W.paper_implosion(nr=200)
+    ring = imp.fields["lam"] == 1.0
+    r, _ = W.grid(200, 1, 0.0, 0.1)
+    assert np.array_equal(ring, r > 0.098) and ring.sum() == 4
+    exp_ = W.paper_explosion(0.015, 0.3, 600)
+    core = exp_.fields["lam"] == 1.0
+    for w, sel, sign in ((imp, ring, -1.0), (exp_, core, 1.0)):
+        assert np.all(w.fields["rho"][sel] == gold["rho"]) and np.all(w.fields["T"][sel] == gold["T"])
+        assert np.all(w.fields["ur"][sel] == sign * abs(gold["u_r"]))
+        assert np.all(w.fields["rho"][~sel] == 1.0) and np.all(w.fields["T"][~sel] == 1.0)
+        assert np.all(w.fields["ur"][~sel] == 0.0) and np.all(w.fields["uth"] == 0.0)
