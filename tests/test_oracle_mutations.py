@@ -129,6 +129,15 @@ MUTANTS = [
      "return lam[(long)(m > 0 ? m - 1 : 0) * p->nr + j];"),
     ("lambda theta wrap above", "return lam[(long)(m < p->ntheta - 1 ? m + 1 : 0) * p->nr + j];",
      "return lam[(long)(m < p->ntheta - 1 ? m + 1 : p->ntheta - 1) * p->nr + j];"),
+    ("F_k T^4 coefficient", "double num = 48.0 * T * T * T * T", "double num = 24.0 * T * T * T * T"),
+    ("F_k T^3 coefficient", "- 6.0 * (a + b + c) * T * T * T", "- 8.0 * (a + b + c) * T * T * T"),
+    ("F_k T^2 term sign", "+ (a * b + b * c + c * a) * T * T", "- (a * b + b * c + c * a) * T * T"),
+    ("F_k denominator without x_k", "double den = x[k] * (x[k] - a)", "double den = (x[k] - a)"),
+    ("F_k cyclic index", "int k3 = k + 3 > 4 ? k + 3 - 4 : k + 3;", "int k3 = k + 3 > 4 ? k + 2 - 4 : k + 3;"),
+    ("x = v instead of v^2", "x[k] = v[k - 1] * v[k - 1];", "x[k] = v[k - 1];"),
+    ("macro: lambda output not copied", "if (lam_out) lam_out[s] = lam[s];", "if (lam_out) lam_out[s] = 0.0;"),
+    ("macro: u_r and u_theta swapped", "if (ur) ur[s] = b;\n            if (uth) uth[s] = c;",
+     "if (ur) ur[s] = c;\n            if (uth) uth[s] = b;"),
 ]
 
 ZND_MUTANTS = [
