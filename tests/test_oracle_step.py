@@ -4,6 +4,7 @@ equivariance of the Cartesian-fixed velocity set on a polar grid, the
 direction and speed of pure advection, and upwind transport of lambda.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -397,3 +398,20 @@ def test_run_equals_repeated_steps(orc):
     for k in ("rho", "ur", "uth", "T", "lam"):
         assert np.array_equal(out[k], ref[k]), k
     assert not np.array_equal(ref["rho"], w.fields["rho"])
+
+
+def test_results_do_not_depend_on_the_thread_count(orc):
+    """The oracle parallelises over theta rows only and each site is computed
+    alone, so one thread and several give the same bits (the parity tests
+    run it with however many cores the host has)."""
+    w = W.random_smooth(40, 24, seed=8, amp=0.15, dt=2e-4, omega1=2.0, omega2=3.0)
+    p = _p(orc, w)
+    try:
+        assert orc.set_threads(1) == 1
+        one = orc.run(p, w.fields, 5)
+        orc.set_threads(3)
+        three = orc.run(p, w.fields, 5)
+    finally:
+        orc.set_threads(int(os.environ.get("ORACLE_THREADS", "0")))  # the session's setting
+    for k in ("rho", "ur", "uth", "T", "lam"):
+        assert np.array_equal(one[k], three[k]), k
