@@ -143,7 +143,9 @@ size_t dbm_state_bytes(const dbm_params *p);
 int dbm_plan_items(int32_t nr, int32_t ntheta, int32_t width, int32_t slots, int32_t rows_requested,
                    int32_t *rows_per_item, int64_t *items);
 
-/* Bind a simulation to caller device memory dev_buf (dev_bytes >=
+/* Runtime call; no passage of the paper corresponds to it (the paper
+ * describes the update, not its bookkeeping).
+ * Bind a simulation to caller device memory dev_buf (dev_bytes >=
  * dbm_state_bytes(p), 256-byte aligned, on the current device).  Uploads the
  * geometry tables and clears the buffer on the legacy default stream and
  * waits for that stream only (work in flight on non-blocking streams goes on;
@@ -152,23 +154,34 @@ int dbm_plan_items(int32_t nr, int32_t ntheta, int32_t width, int32_t slots, int
  * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (buffer too small), DBM_ECUDA. */
 int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out);
 
-/* Release the handle (not dev_buf).  Waits for no GPU work: the caller must
- * not destroy a handle whose work is still queued. */
+/* Runtime call; no passage of the paper corresponds to it.
+ * Release the handle (not dev_buf).  First waits until the GPU has finished
+ * the last work enqueued on the handle's buffers: the handle's own calls
+ * (steps, init, moments, non-equilibrium moments) and the batched steps in
+ * which it was active, so dev_buf may be reused once this returns.  Work the
+ * caller captured into its own CUDA graphs is the caller's to finish.
+ * Errors: DBM_EINVAL (NULL), DBM_ECUDA (that work failed; the handle is
+ * released all the same). */
 int dbm_destroy(dbm_t *h);
 
 /* Set the state at t = 0 from host fields rho, u_r, u_theta, T, lambda
  * ([ntheta][nr] doubles each, caller-owned, read during the call): f = f^eq
- * of the fields at every site, lambda copied (reading: the paper gives
- * macroscopic initial data only).  Enqueued on `stream`; the host arrays are
- * copied before the call returns.  Resets the step counter.
- * Errors: DBM_EINVAL (NULL array, rho <= 0 or T <= 0 or non-finite value),
- * DBM_ECUDA. */
+ * (Eq. feq, Sec. II.B) of the fields at every site, lambda copied (reading:
+ * the paper gives macroscopic initial data only).  f^eq is evaluated in the
+ * state's precision with the arithmetic of the step's own equilibrium.  The
+ * fields are copied to the device and checked there by the init kernel;
+ * the call synchronises `stream` once at the end, so the host arrays may be
+ * reused on return.  Resets the step counter.
+ * Errors: DBM_EINVAL (NULL array, or some rho <= 0, T <= 0 or non-finite
+ * value: the state is then undefined until the next init), DBM_ECUDA. */
 int dbm_init_state(dbm_t *h, const double *rho, const double *ur, const double *uth,
                    const double *T, const double *lam, void *stream);
 
 /* As dbm_init_state with device-resident fields: d_fields points to
  * 5 * ntheta * nr doubles laid out [field][ntheta][nr] in the order rho, u_r,
- * u_theta, T, lambda (read by the GPU in stream order). */
+ * u_theta, T, lambda (read by the GPU in stream order).  Asynchronous: an
+ * invalid value is reported as DBM_EINVAL by the next dbm_status or
+ * dbm_moments. */
 int dbm_init_state_device(dbm_t *h, const double *d_fields, void *stream);
 
 /* Enqueue nsteps time steps (Eq. LB_evolution_equation + Eq. Eqlambda) on
@@ -178,12 +191,15 @@ int dbm_step(dbm_t *h, int64_t nsteps, void *stream);
 
 /* Macroscopic fields of the current state, copied to host arrays (any may be
  * NULL): rho = sum f, u = sum f v / rho in polar components, T = sum f
- * (v - u)^2 / (2 rho) (Sec. II.B), lambda.  Moments are evaluated in FP64
- * from f.  totals (may be NULL) receives the FP64 area-weighted sums
- * {mass, momentum_x, momentum_y, energy}, energy = rho T + rho u^2 / 2,
- * weight r dr dtheta.  Synchronises `stream`.
+ * (v - u)^2 / (2 rho) (Sec. II.B), lambda.  Each site's moments are
+ * evaluated in the state's precision: FP64 states in FP64; FP32 states in
+ * FP32 ring by ring, the very values the step computes, widened to double.
+ * totals (may be NULL) receives the area-weighted sums {mass, momentum_x,
+ * momentum_y, energy}, energy = rho T + rho u^2 / 2, weight r dr dtheta,
+ * accumulated over sites in FP64.  Synchronises `stream`.
  * Errors: DBM_ENONFINITE (some moment is NaN/inf; outputs still written),
- * DBM_ETIMEOUT (a step kernel's bounded wait expired), DBM_ECUDA. */
+ * DBM_ETIMEOUT (a step kernel's bounded wait expired), DBM_EINVAL (the last
+ * dbm_init_state_device found an invalid field value), DBM_ECUDA. */
 int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, double *lam,
                 double totals[4], void *stream);
 
@@ -210,10 +226,23 @@ int dbm_noneq_device(dbm_t *h, double *d_out, void *stream);
 /* Steps taken since the last init or import. */
 int64_t dbm_steps_done(const dbm_t *h);
 
+/* Runtime call; no passage of the paper corresponds to it.
+ * Host-only: device addresses of the current state inside the handle's
+ * buffer, for callers that read it in place (for example
+ * dbm_totals_noalloc).  *d_f: f[33][ntheta][ld] and *d_lam: lam[ntheta][ld]
+ * in the handle's precision, ld = nr rounded up to a multiple of 32 (*ld);
+ * lam holds the stored reaction variable as in dbm_export_state.  The state
+ * alternates between two buffers: the addresses are those the next step
+ * reads, valid for work enqueued (in stream order) before the next
+ * dbm_step, dbm_batch_step, init or import of the handle.  Any output may be
+ * NULL.  Errors: DBM_EINVAL (NULL handle). */
+int dbm_state_device(const dbm_t *h, const void **d_f, const void **d_lam, int64_t *ld);
+
 /* Synchronise `stream` and report the sticky device status word: DBM_OK,
  * DBM_ETIMEOUT (a bounded wait in a step kernel expired), DBM_EDEVICE (a
  * device-side self-check failed and the step skipped the offending copy or
- * store; dbm_last_error says which) or DBM_ECUDA. */
+ * store; dbm_last_error says which), DBM_EINVAL (the last init found an
+ * invalid field value) or DBM_ECUDA. */
 int dbm_status(dbm_t *h, void *stream);
 
 /* Checkpoint: copy the raw state to host memory.  f receives 33 * ntheta * nr
@@ -269,7 +298,7 @@ int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_ste
 
 /* ---- allocation-free conservation totals -------------------------------- */
 /*
- * The paper has no counterpart to this entry point.  It computes the same FP64
+ * The paper has no counterpart to this entry point.  It computes the same
  * totals as dbm_moments for callers that cannot hand the library any device
  * scratch memory: a component holding only raw device pointers to a state that
  * another component owns (a checkpoint writer or a monitoring thread), or code
@@ -279,23 +308,30 @@ int dbm_autotune(dbm_t *h, int steps, void *stream, int *best, float *ms_per_ste
  * per theta row) is a static device array of DBM_NOALLOC_MAX_ROWS rows
  * (512 KB) that every GPU loading the library holds until the process exits.
  *
- *   d_f       device array f[33][ntheta][nr] in p->precision (float or double),
- *             the layout dbm_export_state writes; read in stream order.
+ *   d_f       device array f[33][ntheta][ld] in p->precision (float or double):
+ *             a live state in place (dbm_state_device gives its address and
+ *             ld) or the unpadded layout dbm_export_state writes (ld = nr);
+ *             read in stream order.  Each site's sums are taken as dbm_moments
+ *             takes them for that precision, accumulated in FP64.
+ *   ld        elements between consecutive theta rows, >= nr; 0 means nr.
  *   d_totals  device array of 4 doubles receiving {mass, momentum_x,
  *             momentum_y, energy}, area-weighted as in dbm_moments.
  *   stream    cudaStream_t as void* (NULL: legacy default stream); the call
  *             only enqueues two kernels and returns.
  *
- * The first call on a device looks up the device address of the static array
- * with that device current; make that first call before any stream capture.
- * All calls share the one array and it keeps the last call's contents; each
- * call rewrites every row it reads, so nothing needs clearing, but calls whose
- * work overlaps on the GPU (for example on two concurrent streams) race on it.
- * Errors: DBM_EINVAL (NULL pointer or invalid grid/precision), DBM_ENOMEM
- * (ntheta > DBM_NOALLOC_MAX_ROWS: the state does not fit the static scratch),
- * DBM_ECUDA (symbol lookup or launch failed). */
+ * The first call on a device (and again after that device's context was
+ * replaced, e.g. by cudaDeviceReset) looks up the device address of the
+ * static array with that device current; make that first call before any
+ * stream capture.  All calls share the one array and it keeps the last
+ * call's contents; each call rewrites every row it reads, so nothing needs
+ * clearing, but calls whose work overlaps on the GPU (for example on two
+ * concurrent streams) race on it.
+ * Errors: DBM_EINVAL (NULL pointer, ld < nr, invalid grid or precision),
+ * DBM_ENOMEM (ntheta > DBM_NOALLOC_MAX_ROWS: the state does not fit the
+ * static scratch), DBM_ECUDA (symbol lookup or launch failed; the failure
+ * is recorded for dbm_last_error). */
 #define DBM_NOALLOC_MAX_ROWS 16384
-int dbm_totals_noalloc(const dbm_params *p, const void *d_f, double *d_totals, void *stream);
+int dbm_totals_noalloc(const dbm_params *p, const void *d_f, int64_t ld, double *d_totals, void *stream);
 
 /* ---- batches: many uneven simulations, one persistent launch per step ---- */
 /*
@@ -309,6 +345,9 @@ int dbm_totals_noalloc(const dbm_params *p, const void *d_f, double *d_totals, v
  * simulation is exactly the single-instance update (same kernel body).
  * All simulations of a batch share one precision.  While attached, a
  * simulation must not be stepped on its own.
+ *
+ * Batches and the server below are runtime machinery (scheduling many
+ * simulations on one GPU); no passage of the paper corresponds to them.
  */
 typedef struct dbm_batch_s dbm_batch_t;
 
@@ -316,11 +355,6 @@ typedef struct dbm_batch_s dbm_batch_t;
  * max_items work items (0 if an argument is invalid). */
 size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
 
-/* Create a batch on caller device memory (256-byte aligned, >=
- * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16; -1 =
- * scaled to each simulation: 16 up to 512 theta rows, 32 up to 1024, else 64).
- * Allocates a pinned host staging buffer for the tables.  Synchronous.
- * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
 /* Host-only: the work items of a batched step (what dbm_batch_step launches
  * after a commit).  Slot s holds an nr[s] x ntheta[s] simulation (nr[s] = 0:
  * empty), cut into strips of `width` radial sites (the kernel's W) by runs of
@@ -336,10 +370,17 @@ size_t dbm_batch_bytes(int max_slots, int64_t max_items, int precision);
 int dbm_batch_plan(int32_t nslots, const int32_t *nr, const int32_t *ntheta, const int32_t *rows_per_item,
                    int32_t width, int32_t grid, int64_t max_items, int32_t *items, int64_t *n_items);
 
+/* Create a batch on caller device memory (256-byte aligned, >=
+ * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16; -1 =
+ * scaled to each simulation: 16 up to 512 theta rows, 32 up to 1024, else 64).
+ * Allocates a pinned host staging buffer for the tables.  Synchronous.
+ * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
 int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
                      void *dev_buf, size_t dev_bytes, dbm_batch_t **out);
 
-/* Free the batch (not the attached simulations or dev_buf). */
+/* Runtime call; no passage of the paper corresponds to it.  Free the batch
+ * (not the attached simulations or dev_buf) after waiting for the batched
+ * steps already enqueued, which read its tables in dev_buf. */
 int dbm_batch_destroy(dbm_batch_t *b);
 
 /* Attach simulation h to a free slot to advance nsteps steps from the batch's
@@ -453,7 +494,8 @@ size_t dbm_server_min_bytes(const dbm_server_config *cfg);
 int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_bytes,
                       dbm_server_t **out);
 
-/* Queue a simulation: params (precision must match the server's), initial
+/* Runtime call; no passage of the paper corresponds to it.
+ * Queue a simulation: params (precision must match the server's), initial
  * fields (copied before return), nsteps.  *ticket identifies it.
  * Errors: DBM_EINVAL, DBM_ECFL, DBM_ENOMEM (larger than the whole pool),
  * DBM_EBUSY (queue full), or the error that ended the server's work.
@@ -468,7 +510,8 @@ int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_
 int dbm_submit(dbm_server_t *s, const dbm_params *p, const dbm_fields *init, int64_t nsteps,
                uint64_t *ticket);
 
-/* Wait up to timeout_us (0: do not wait, < 0: forever) for a request.  On
+/* Runtime call; no passage of the paper corresponds to it.
+ * Wait up to timeout_us (0: do not wait, < 0: forever) for a request.  On
  * DBM_OK *out holds its result (status inside) and the ticket is consumed;
  * free the arrays with dbm_result_free.  DBM_ENOTREADY (timeout_us = 0 and
  * still queued or running), DBM_ETIMEOUT, DBM_ENOTFOUND. */

@@ -41,6 +41,14 @@ int cuda_fail(cudaError_t e, const char *what)
     return DBM_ECUDA;
 }
 
+}  // namespace
+
+namespace dbm {
+int record_cuda_failure(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+}  // namespace dbm
+
+namespace {
+
 #define CK(call)                                              \
     do {                                                      \
         cudaError_t e_ = (call);                              \
@@ -149,11 +157,34 @@ struct dbm_s {
     cudaGraphExec_t graph;    // GRAPH_STEPS steps starting from buffer 0
     int device;
     bool tmap_ok;             // tensor maps encoded (tensor-TMA variants usable)
+    cudaEvent_t done;         // recorded after the last work that touches the buffers
+    int host_word[2];         // host side of small device-to-host status copies
 };
 
 namespace {
 
 constexpr int GRAPH_STEPS = 32;
+
+// Second word of the status region: set by the init kernel when an initial
+// field value is invalid (rho <= 0, T <= 0, not finite).
+int *bad_input_word(dbm_t *h) { return reinterpret_cast<int *>(h->buf + h->L.status) + 1; }
+
+int bad_input_fail()
+{
+    snprintf(g_last_error, sizeof(g_last_error),
+             "initial fields: some rho <= 0, T <= 0 or non-finite value (state undefined until the next init)");
+    return DBM_EINVAL;
+}
+
+// Record that work touching the handle's buffers was enqueued on `s`, so
+// that dbm_destroy can wait for it.  Not while `s` is being captured into a
+// graph (the work then runs when the caller launches the graph).
+void note_work(dbm_t *h, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+    cudaEventRecord(h->done, s);
+}
 
 // cuTensorMapEncodeTiled from the driver, looked up once (no link to libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -548,6 +579,13 @@ int dbm_plan_items(int32_t nr, int32_t ntheta, int32_t width, int32_t slots, int
     return DBM_OK;
 }
 
+static void free_handle(dbm_t *h)
+{
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->done) cudaEventDestroy(h->done);
+    delete h;
+}
+
 int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out)
 {
     if (!p || !dev_buf || !out) return DBM_EINVAL;
@@ -568,6 +606,7 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
     h->ld = padded_ld(p->nr);
     h->plane = (long long)h->ld * p->ntheta;
     cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete h;
         return cuda_fail(e, "dbm_create: device query");
@@ -579,7 +618,7 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
         if (fb != v0) rc = configure_launch(h, fb);
     }
     if (rc != DBM_OK) {
-        delete h;
+        free_handle(h);
         return rc;
     }
     // cleared on the legacy stream, which the library's and the server's
@@ -588,12 +627,12 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
     e = cudaMemset(dev_buf, 0, L.total);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) {
-        delete h;
+        free_handle(h);
         return cuda_fail(e, "dbm_create: clear buffer");
     }
     rc = p->precision == DBM_FP64 ? upload_tables<double>(h) : upload_tables<float>(h);
     if (rc != DBM_OK) {
-        delete h;
+        free_handle(h);
         return rc;
     }
     *out = h;
@@ -603,43 +642,49 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
 int dbm_destroy(dbm_t *h)
 {
     if (!h) return DBM_EINVAL;
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    delete h;
+    // the last work enqueued on the handle's buffers (its own calls, and
+    // batched steps in which it was active) must finish before the caller
+    // may reuse them
+    const cudaError_t e = cudaEventSynchronize(h->done);
+    free_handle(h);
+    if (e != cudaSuccess) return cuda_fail(e, "dbm_destroy: wait for the handle's work");
     return DBM_OK;
 }
 
-static int launch_init_from(dbm_t *h, const double *d_fields, cudaStream_t s)
+}  // extern "C"
+
+template <typename real>
+static cudaError_t launch_init_as(dbm_t *h, const double *d_fields, cudaStream_t s)
 {
     double Fc[4][4];
     weight_coeffs(h->p.v, Fc);
-    cudaError_t e;
-    if (h->p.precision == DBM_FP64) {
-        InitArgs<double> A;
-        A.fields = d_fields;
-        A.f = reinterpret_cast<double *>(h->buf + h->L.f[0]);
-        A.lam = reinterpret_cast<double *>(h->buf + h->L.lam[0]);
-        A.plane = h->plane;
-        A.nr = h->p.nr;
-        A.ntheta = h->p.ntheta;
-        A.ld = h->ld;
-        A.th_over_pi = theta_span(h->p) / PI / h->p.ntheta;
-        std::memcpy(A.v, h->p.v, sizeof(A.v));
-        std::memcpy(A.Fc, Fc, sizeof(Fc));
-        e = launch_init<double>(A, s);
-    } else {
-        InitArgs<float> A;
-        A.fields = d_fields;
-        A.f = reinterpret_cast<float *>(h->buf + h->L.f[0]);
-        A.lam = reinterpret_cast<float *>(h->buf + h->L.lam[0]);
-        A.plane = h->plane;
-        A.nr = h->p.nr;
-        A.ntheta = h->p.ntheta;
-        A.ld = h->ld;
-        A.th_over_pi = theta_span(h->p) / PI / h->p.ntheta;
-        std::memcpy(A.v, h->p.v, sizeof(A.v));
-        std::memcpy(A.Fc, Fc, sizeof(Fc));
-        e = launch_init<float>(A, s);
+    InitArgs<real> A;
+    std::memset(&A, 0, sizeof(A));
+    A.fields = d_fields;
+    A.f = reinterpret_cast<real *>(h->buf + h->L.f[0]);
+    A.lam = reinterpret_cast<real *>(h->buf + h->L.lam[0]);
+    A.rowtab = reinterpret_cast<const real *>(h->buf + h->L.rowtab);
+    A.bad = bad_input_word(h);
+    A.plane = h->plane;
+    A.nr = h->p.nr;
+    A.ntheta = h->p.ntheta;
+    A.ld = h->ld;
+    for (int k = 0; k < 4; ++k) {
+        A.v[k] = (real)h->p.v[k];
+        for (int c = 0; c < 4; ++c) A.Fc[k][c] = (real)Fc[k][c];
     }
+    return launch_init<real>(A, s);
+}
+
+extern "C" {
+
+// f = f^eq of the device fields into buffer 0; the kernel checks every value
+// and sets the handle's bad-input word (cleared here first) on a bad one.
+static int launch_init_from(dbm_t *h, const double *d_fields, cudaStream_t s)
+{
+    CK(cudaMemsetAsync(bad_input_word(h), 0, sizeof(int), s));
+    const cudaError_t e = h->p.precision == DBM_FP64 ? launch_init_as<double>(h, d_fields, s)
+                                                     : launch_init_as<float>(h, d_fields, s);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
     h->cur = 0;
     h->steps = 0;
@@ -651,25 +696,31 @@ int dbm_init_state(dbm_t *h, const double *rho, const double *ur, const double *
 {
     if (!h || !rho || !ur || !uth || !T || !lam) return DBM_EINVAL;
     const size_t N = (size_t)h->p.nr * h->p.ntheta;
-    for (size_t s = 0; s < N; ++s) {
-        if (!finite_pos(rho[s]) || !finite_pos(T[s]) || !std::isfinite(ur[s]) ||
-            !std::isfinite(uth[s]) || !std::isfinite(lam[s]))
-            return DBM_EINVAL;
-    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Stage the fields in the second f buffer (free before the first step).
+    // Stage the fields in the second f buffer (free before the first step);
+    // the init kernel validates them on the GPU, and one synchronisation at
+    // the end covers the copies (the host arrays may be reused on return)
+    // and the validation result.
     double *stage = reinterpret_cast<double *>(h->buf + h->L.f[1]);
     const double *src[5] = {rho, ur, uth, T, lam};
     for (int c = 0; c < 5; ++c)
         CK(cudaMemcpyAsync(stage + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));  // host arrays may be reused on return
-    return launch_init_from(h, stage, s);
+    int rc = launch_init_from(h, stage, s);
+    if (rc != DBM_OK) return rc;
+    CK(cudaMemcpyAsync(&h->host_word[0], bad_input_word(h), sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    note_work(h, s);
+    if (h->host_word[0] != 0) return bad_input_fail();
+    return DBM_OK;
 }
 
 int dbm_init_state_device(dbm_t *h, const double *d_fields, void *stream)
 {
     if (!h || !d_fields) return DBM_EINVAL;
-    return launch_init_from(h, d_fields, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = launch_init_from(h, d_fields, s);
+    if (rc == DBM_OK) note_work(h, s);
+    return rc;
 }
 
 int dbm_step(dbm_t *h, int64_t nsteps, void *stream)
@@ -694,8 +745,41 @@ int dbm_step(dbm_t *h, int64_t nsteps, void *stream)
             h->steps += 1;
         }
     }
+    note_work(h, s);
     return DBM_OK;
 }
+
+}  // extern "C"
+
+template <typename real>
+static cudaError_t launch_moments_as(dbm_t *h, double *d_out, double *partials, int grid, cudaStream_t s)
+{
+    const dbm_params &p = h->p;
+    MomArgs<real> A;
+    std::memset(&A, 0, sizeof(A));
+    A.f = reinterpret_cast<const real *>(h->buf + h->L.f[h->cur]);
+    A.lam = reinterpret_cast<const real *>(h->buf + h->L.lam[h->cur]);
+    A.out = d_out;
+    A.partials = partials;
+    A.status = reinterpret_cast<int *>(h->buf + h->L.status);
+    A.rowtab = reinterpret_cast<const real *>(h->buf + h->L.rowtab);
+    A.plane = h->plane;
+    A.nr = p.nr;
+    A.ntheta = p.ntheta;
+    A.ld = h->ld;
+    A.r_in = p.r_in;
+    A.dr = (p.r_out - p.r_in) / p.nr;
+    A.dtheta = theta_span(p) / p.ntheta;
+    A.th_over_pi = theta_span(p) / PI / p.ntheta;
+    std::memcpy(A.v, p.v, sizeof(A.v));
+    for (int k = 0; k < 4; ++k) {
+        A.vr[k] = (real)p.v[k];
+        A.v2r[k] = (real)(p.v[k] * p.v[k]);
+    }
+    return launch_moments<real>(A, grid, s);
+}
+
+extern "C" {
 
 static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
 {
@@ -703,43 +787,8 @@ static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
     const long long N = (long long)p.nr * p.ntheta;
     int grid = (int)std::min<long long>((N + 255) / 256, MOMENT_BLOCKS);
     double *partials = reinterpret_cast<double *>(h->buf + h->L.partials);
-    int *status = reinterpret_cast<int *>(h->buf + h->L.status);
-    cudaError_t e;
-    if (p.precision == DBM_FP64) {
-        MomArgs<double> A;
-        A.f = reinterpret_cast<const double *>(h->buf + h->L.f[h->cur]);
-        A.lam = reinterpret_cast<const double *>(h->buf + h->L.lam[h->cur]);
-        A.out = d_out;
-        A.partials = partials;
-        A.status = status;
-        A.plane = h->plane;
-        A.nr = p.nr;
-        A.ntheta = p.ntheta;
-        A.ld = h->ld;
-        A.r_in = p.r_in;
-        A.dr = (p.r_out - p.r_in) / p.nr;
-        A.dtheta = theta_span(p) / p.ntheta;
-        A.th_over_pi = theta_span(p) / PI / p.ntheta;
-        std::memcpy(A.v, p.v, sizeof(A.v));
-        e = launch_moments<double>(A, grid, s);
-    } else {
-        MomArgs<float> A;
-        A.f = reinterpret_cast<const float *>(h->buf + h->L.f[h->cur]);
-        A.lam = reinterpret_cast<const float *>(h->buf + h->L.lam[h->cur]);
-        A.out = d_out;
-        A.partials = partials;
-        A.status = status;
-        A.plane = h->plane;
-        A.nr = p.nr;
-        A.ntheta = p.ntheta;
-        A.ld = h->ld;
-        A.r_in = p.r_in;
-        A.dr = (p.r_out - p.r_in) / p.nr;
-        A.dtheta = theta_span(p) / p.ntheta;
-        A.th_over_pi = theta_span(p) / PI / p.ntheta;
-        std::memcpy(A.v, p.v, sizeof(A.v));
-        e = launch_moments<float>(A, grid, s);
-    }
+    cudaError_t e = p.precision == DBM_FP64 ? launch_moments_as<double>(h, d_out, partials, grid, s)
+                                            : launch_moments_as<float>(h, d_out, partials, grid, s);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
     e = launch_totals(partials, grid, reinterpret_cast<double *>(h->buf + h->L.totals), s);
     if (e != cudaSuccess) return cuda_fail(e, "totals kernel launch");
@@ -784,7 +833,10 @@ static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
 int dbm_noneq_device(dbm_t *h, double *d_out, void *stream)
 {
     if (!h || !d_out) return DBM_EINVAL;
-    return launch_noneq_into(h, d_out, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = launch_noneq_into(h, d_out, s);
+    if (rc == DBM_OK) note_work(h, s);
+    return rc;
 }
 
 int dbm_noneq(dbm_t *h, double *out, void *stream)
@@ -804,7 +856,10 @@ int dbm_noneq(dbm_t *h, double *out, void *stream)
 int dbm_moments_device(dbm_t *h, double *d_out, void *stream)
 {
     if (!h || !d_out) return DBM_EINVAL;
-    return launch_moments_into(h, d_out, static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int rc = launch_moments_into(h, d_out, s);
+    if (rc == DBM_OK) note_work(h, s);
+    return rc;
 }
 
 int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, double *lam,
@@ -822,11 +877,12 @@ int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, doubl
             CK(cudaMemcpyAsync(dst[c], stage + c * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (totals)
         CK(cudaMemcpyAsync(totals, h->buf + h->L.totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    int status = 0;
-    CK(cudaMemcpyAsync(&status, h->buf + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->host_word, h->buf + h->L.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const int status = h->host_word[0];
     if (status & ST_WAIT_TIMEOUT) return DBM_ETIMEOUT;
     if (device_check_status(status) != DBM_OK) return DBM_EDEVICE;
+    if (h->host_word[1] != 0) return bad_input_fail();
     if (status & ST_NONFINITE) {
         CK(cudaMemsetAsync(h->buf + h->L.status, 0, sizeof(int), s));
         CK(cudaStreamSynchronize(s));
@@ -837,15 +893,27 @@ int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, doubl
 
 int64_t dbm_steps_done(const dbm_t *h) { return h ? h->steps : -1; }
 
+int dbm_state_device(const dbm_t *h, const void **d_f, const void **d_lam, int64_t *ld)
+{
+    if (!h) return DBM_EINVAL;
+    if (d_f) *d_f = h->buf + h->L.f[h->cur];
+    if (d_lam) *d_lam = h->buf + h->L.lam[h->cur];
+    if (ld) *ld = h->ld;
+    return DBM_OK;
+}
+
 int dbm_status(dbm_t *h, void *stream)
 {
     if (!h) return DBM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int status = 0;
-    CK(cudaMemcpyAsync(&status, h->buf + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->host_word, h->buf + h->L.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    const int status = h->host_word[0];
     if (status & ST_WAIT_TIMEOUT) return DBM_ETIMEOUT;
-    return device_check_status(status);
+    const int rc = device_check_status(status);
+    if (rc != DBM_OK) return rc;
+    if (h->host_word[1] != 0) return bad_input_fail();
+    return DBM_OK;
 }
 
 int dbm_export_state(dbm_t *h, void *f, void *lam, int64_t *steps, void *stream)
@@ -996,6 +1064,7 @@ struct dbm_batch_s {
     std::vector<int> par0;
     unsigned char *stage;     // pinned host staging of the slot and item tables
     cudaEvent_t stage_ev;
+    cudaEvent_t done;         // recorded after the last batched steps enqueued
     bool stage_pending;
     long long T;              // host mirror of the device step counter
     int n_items;
@@ -1009,6 +1078,13 @@ struct dbm_batch_s {
 };
 
 namespace {
+
+void note_batch_work(dbm_batch_t *b, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+    cudaEventRecord(b->done, s);
+}
 
 struct BatchLayout {
     size_t slot_bytes, slots, items, nitems, T, total;
@@ -1264,10 +1340,13 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
     if (e == cudaSuccess) e = cudaHostAlloc(&b->stage, L.items + (size_t)max_items * sizeof(int4) + 256,
                                             cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(dev_buf, 0, L.total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         if (b->stage) cudaFreeHost(b->stage);
+        if (b->stage_ev) cudaEventDestroy(b->stage_ev);
+        if (b->done) cudaEventDestroy(b->done);
         delete b;
         return cuda_fail(e, "dbm_batch_create");
     }
@@ -1282,8 +1361,10 @@ int dbm_batch_destroy(dbm_batch_t *b)
 {
     if (!b) return DBM_EINVAL;
     if (b->stage_pending) cudaEventSynchronize(b->stage_ev);
+    cudaEventSynchronize(b->done);  // queued batched steps read the tables
     if (b->graph) cudaGraphExecDestroy(b->graph);
     cudaEventDestroy(b->stage_ev);
+    cudaEventDestroy(b->done);
     cudaFreeHost(b->stage);
     delete b;
     return DBM_OK;
@@ -1432,7 +1513,12 @@ int dbm_batch_step(dbm_batch_t *b, int64_t nsteps, void *stream)
             b->T += k;
         }
     }
-    for (int s = 0; s < b->max_slots; ++s) batch_account(b, s, t0, b->T);
+    for (int s = 0; s < b->max_slots; ++s) {
+        // a simulation active in these steps: its dbm_destroy waits for them
+        if (b->inst[s] && b->start[s] < b->T && b->end[s] > t0) note_work(b->inst[s], st);
+        batch_account(b, s, t0, b->T);
+    }
+    note_batch_work(b, st);
     return DBM_OK;
 }
 

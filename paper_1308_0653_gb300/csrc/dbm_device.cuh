@@ -307,6 +307,43 @@ template <> struct LamStore<float> {
 };
 
 // ---------------------------------------------------------------------------
+// A site's moments from its 33 f (Sec. II.B), ring by ring in Cartesian
+// components: rho = sum f, (jx, jy) = sum f v, e2 = sum f |v|^2.  Within a
+// ring the 8 directions are summed pairwise and opposite directions are
+// differenced first (exact for nearly equal values).  Shared by the step,
+// the FP32 moments and the allocation-free totals, so all see the same values.
+// ---------------------------------------------------------------------------
+template <typename real>
+struct RingSpeeds {
+    real v[4], v2[4];  // ring speeds v_k and their squares
+};
+
+template <typename real>
+__device__ __forceinline__ void ring_moments(const real (&f)[NV], const real (&v)[4], const real (&v2)[4],
+                                             real &rho, real &jx, real &jy, real &e2)
+{
+    using O = Op<real>;
+    const real H = real(0.70710678118654752440);  // cos(pi/4)
+    rho = f[0];
+    jx = real(0);
+    jy = real(0);
+    e2 = real(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const real *g = &f[1 + 8 * k];
+        const real s0 = O::add(O::add(O::add(g[0], g[4]), O::add(g[2], g[6])),
+                               O::add(O::add(g[1], g[5]), O::add(g[3], g[7])));
+        const real a = O::sub(g[1], g[5]), b = O::sub(g[3], g[7]);
+        const real sx = O::fma(H, O::sub(a, b), O::sub(g[0], g[4]));
+        const real sy = O::fma(H, O::add(a, b), O::sub(g[2], g[6]));
+        rho = O::add(rho, s0);
+        jx = O::fma(v[k], sx, jx);
+        jy = O::fma(v[k], sy, jy);
+        e2 = O::fma(v2[k], s0, e2);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One site's update (Eq. LB_evolution_equation, Eq. Eqlambda), all 33
 // velocities unrolled.  sp/sc/sn: shared-memory buffers of rows m-1, m, m+1;
 // col = HALO + tx.  Velocity (k, i) has Cartesian direction i pi / 4, so its
@@ -335,20 +372,8 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
 
     // --- a2: moments, ring by ring (Cartesian components) ------------------
     //     rho = sum f, rho u = sum f v, e2 = sum f v^2, T = (e2/rho - u^2)/2
-    real rho = f[0], jx = real(0), jy = real(0), e2 = real(0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const real *g = &f[1 + 8 * k];
-        const real s0 = O::add(O::add(O::add(g[0], g[4]), O::add(g[2], g[6])),
-                               O::add(O::add(g[1], g[5]), O::add(g[3], g[7])));
-        const real a = O::sub(g[1], g[5]), b = O::sub(g[3], g[7]);
-        const real sx = O::fma(H, O::sub(a, b), O::sub(g[0], g[4]));
-        const real sy = O::fma(H, O::add(a, b), O::sub(g[2], g[6]));
-        rho = O::add(rho, s0);
-        jx = O::fma(A.v[k], sx, jx);
-        jy = O::fma(A.v[k], sy, jy);
-        e2 = O::fma(A.v2[k], s0, e2);
-    }
+    real rho, jx, jy, e2;
+    ring_moments<real>(f, A.v, A.v2, rho, jx, jy, e2);
     const real inv_rho = O::rcp(rho);
     const real ux = O::mul(jx, inv_rho), uy = O::mul(jy, inv_rho);
     const real u2 = O::fma(ux, ux, O::mul(uy, uy));
@@ -1060,21 +1085,17 @@ static __global__ void rcp_selftest_kernel(const float *x, float *approx, float 
 }
 
 // ---------------------------------------------------------------------------
-// Initial state: f = f^eq(rho, u, T) (Eq. feq) in FP64, rounded once to real.
-// fields: [5][ntheta][nr] doubles (rho, u_r, u_theta, T, lambda).
+// Initial state: f = f^eq(rho, u, T) (Eq. feq) of the initial fields, lambda
+// stored.  fields: [5][ntheta][nr] doubles (rho, u_r, u_theta, T, lambda).
+// f^eq is evaluated in the state's precision with the arithmetic of the
+// step's own equilibrium (weights F_k by Horner, expansion coefficients from
+// u^2 / T, xi = v_k (e_i . u) / T), from the fields rounded to `real` and the
+// row's cos / sin of the geometry table; opposite directions share the even
+// and odd parts of the expansion.  Every value is checked (rho > 0, T > 0,
+// all finite): a block that finds a bad one sets *bad, which the host reports
+// as DBM_EINVAL (the state is then undefined).
 // ---------------------------------------------------------------------------
-template <typename real>
-struct InitArgs {
-    const double *fields;
-    real *f;
-    real *lam;
-    long long plane;
-    int nr, ntheta, ld;
-    double th_over_pi;  // theta_m / pi per row: 2 / ntheta, or 1 / (4 ntheta) in a sector
-    double v[4];
-    double Fc[4][4];
-};
-
+// Cartesian direction cosines of the 8 directions i pi / 4 (FP64 kernels).
 __device__ __forceinline__ void cart_dirs(double (&cx)[8], double (&cy)[8])
 {
     const double H = 0.70710678118654752440;
@@ -1088,44 +1109,83 @@ __device__ __forceinline__ void cart_dirs(double (&cx)[8], double (&cy)[8])
 }
 
 template <typename real>
-__global__ void init_kernel(const InitArgs<real> A)
+struct InitArgs {
+    const double *fields;
+    real *f;
+    real *lam;
+    const real *rowtab;  // [ntheta][16]: cos, sin of (i pi/4 - theta_m)
+    int *bad;
+    long long plane;
+    int nr, ntheta, ld;
+    real v[4];
+    real Fc[4][4];
+};
+
+template <typename real>
+__global__ void __launch_bounds__(256) init_kernel(const InitArgs<real> A)
 {
+    using O = Op<real>;
+    const real H = real(0.70710678118654752440);
+    const real one = real(1), half = real(0.5);
     const long long N = (long long)A.nr * A.ntheta;
-    double cx[8], cy[8];
-    cart_dirs(cx, cy);
+    bool bad = false;
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
-        const double rho = A.fields[s], ur = A.fields[N + s], uth = A.fields[2 * N + s];
-        const double T = A.fields[3 * N + s], lam = A.fields[4 * N + s];
-        double sth, cth;
-        sincospi(A.th_over_pi * m, &sth, &cth);
-        const double ux = ur * cth - uth * sth, uy = ur * sth + uth * cth;
-        const double u2 = ux * ux + uy * uy;
-        double F[4], Fsum = 0.0;
-        for (int k = 0; k < 4; ++k) {
-            F[k] = T * (A.Fc[k][0] + T * (A.Fc[k][1] + T * (A.Fc[k][2] + T * A.Fc[k][3])));
-            Fsum += F[k];
+        const double rho_d = A.fields[s], ur_d = A.fields[N + s], uth_d = A.fields[2 * N + s];
+        const double T_d = A.fields[3 * N + s], lam_d = A.fields[4 * N + s];
+        if (!(rho_d > 0.0) || !(T_d > 0.0) || !isfinite(rho_d) || !isfinite(T_d) || !isfinite(ur_d) ||
+            !isfinite(uth_d) || !isfinite(lam_d)) {
+            bad = true;
+            continue;
         }
-        const double F0 = 1.0 - 8.0 * Fsum;
-        const double hh = 0.5 * u2 / T;
-        const double A0 = 1.0 - hh + 0.5 * hh * hh, A1 = 1.0 - hh, A2 = 0.5 * A1;
-        real *out = A.f + (long long)m * A.ld + j;
-        out[0] = (real)(rho * F0 * A0);
+        const real rho = (real)rho_d, ur = (real)ur_d, uth = (real)uth_d, T = (real)T_d;
+        const real cth = A.rowtab[(long long)m * 16], sth = -A.rowtab[(long long)m * 16 + 8];
+        const real ux = O::fma(ur, cth, -O::mul(uth, sth));
+        const real uy = O::fma(ur, sth, O::mul(uth, cth));
+        const real u2 = O::fma(ux, ux, O::mul(uy, uy));
+        const real inv_T = O::rcp(T);
+        real F[4], Fsum = real(0);
+#pragma unroll
         for (int k = 0; k < 4; ++k) {
-            for (int i = 0; i < 8; ++i) {
-                const double xi = A.v[k] * (cx[i] * ux + cy[i] * uy) / T;
-                const double poly = A0 + xi * (A1 + xi * (A2 + xi * (1.0 / 6.0 + xi * (1.0 / 24.0))));
-                out[(long long)(1 + 8 * k + i) * A.plane] = (real)(rho * F[k] * poly);
+            F[k] = O::mul(T, O::fma(T, O::fma(T, O::fma(T, A.Fc[k][3], A.Fc[k][2]), A.Fc[k][1]), A.Fc[k][0]));
+            Fsum = O::add(Fsum, F[k]);
+        }
+        const real F0 = O::fma(real(-8), Fsum, one);
+        const real hh = O::mul(O::mul(half, u2), inv_T);
+        const real A1 = O::sub(one, hh);
+        const real A0 = O::fma(O::mul(half, hh), hh, A1);
+        const real A2 = O::mul(half, A1);
+        const real wx = O::mul(ux, inv_T), wy = O::mul(uy, inv_T);
+        const real w[4] = {wx, O::mul(H, O::add(wx, wy)), wy, O::mul(H, O::sub(wy, wx))};
+        real *out = A.f + (long long)m * A.ld + j;
+        out[0] = O::mul(O::mul(rho, F0), A0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const real rF = O::mul(rho, F[k]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const real xi = O::mul(A.v[k], w[i]);  // direction i + 4 has -xi
+                const real x2 = O::mul(xi, xi);
+                const real Ev = O::fma(x2, O::fma(x2, real(1.0 / 24.0), A2), A0);
+                const real Od = O::mul(xi, O::fma(x2, real(1.0 / 6.0), A1));
+                out[(long long)(1 + 8 * k + i) * A.plane] = O::mul(rF, O::add(Ev, Od));
+                out[(long long)(5 + 8 * k + i) * A.plane] = O::mul(rF, O::sub(Ev, Od));
             }
         }
-        A.lam[(long long)m * A.ld + j] = (real)LamStore<real>::from_lambda(lam);
+        A.lam[(long long)m * A.ld + j] = (real)LamStore<real>::from_lambda(lam_d);
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(A.bad, 1);
 }
 
 // ---------------------------------------------------------------------------
-// Moments (Sec. II.B) in FP64 from f, plus per-block partial sums of the
-// area-weighted totals {mass, momentum x, momentum y, energy}.
+// Moments (Sec. II.B) from f, plus per-block partial sums of the
+// area-weighted totals {mass, momentum x, momentum y, energy}, summed in FP64
+// across sites.  FP64 states: every site in FP64.  FP32 states: each site's
+// rho, rho u and sum f v^2 in FP32, ring by ring exactly as the step computes
+// them (ring_moments), u and T from those in FP32; the outputs are those
+// values widened to double (the FP32 state itself carries ~6e-8 relative
+// rounding per value, so FP64 per-site arithmetic would add no accuracy).
 // out: [5][ntheta][nr] doubles; partials: [gridDim.x][4] (scratch).
 // ---------------------------------------------------------------------------
 template <typename real>
@@ -1135,60 +1195,102 @@ struct MomArgs {
     double *out;
     double *partials;
     int *status;
+    const real *rowtab;  // [ntheta][16] (FP32 moments)
     long long plane;
     int nr, ntheta, ld;
     double r_in, dr, dtheta;
     double th_over_pi;  // theta_m / pi per row
     double v[4];
+    real vr[4], v2r[4];  // ring speeds and squares in real (FP32 moments)
 };
 
 template <typename real>
 __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
 {
     const long long N = (long long)A.nr * A.ntheta;
-    double cx[8], cy[8];
-    cart_dirs(cx, cy);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     bool bad = false;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
-        const real *fp = A.f + (long long)m * A.ld + j;
-        double fv[NV];
-        for (int q = 0; q < NV; ++q) fv[q] = (double)fp[(long long)q * A.plane];
-        double rho = fv[0], jx = 0.0, jy = 0.0;
-        for (int k = 0; k < 4; ++k)
-            for (int i = 0; i < 8; ++i) {
-                const double fq = fv[1 + 8 * k + i];
-                rho += fq;
-                jx += fq * A.v[k] * cx[i];
-                jy += fq * A.v[k] * cy[i];
+    if constexpr (sizeof(real) == 4) {
+        using O = Op<float>;
+        for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+             s += (long long)gridDim.x * blockDim.x) {
+            const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
+            const float *fp = A.f + (long long)m * A.ld + j;
+            float fv[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) fv[q] = fp[(long long)q * A.plane];
+            float rho, jx, jy, e2;
+            ring_moments<float>(fv, A.vr, A.v2r, rho, jx, jy, e2);
+            const float inv_rho = O::rcp(rho);
+            const float ux = O::mul(jx, inv_rho), uy = O::mul(jy, inv_rho);
+            const float u2 = O::fma(ux, ux, O::mul(uy, uy));
+            const float T = O::mul(0.5f, O::sub(O::mul(e2, inv_rho), u2));
+            const float cth = A.rowtab[(long long)m * 16], sth = -A.rowtab[(long long)m * 16 + 8];
+            const float ur = O::fma(ux, cth, O::mul(uy, sth));
+            const float uth = O::fma(uy, cth, -O::mul(ux, sth));
+            const double lam = LamStore<float>::to_lambda((double)A.lam[(long long)m * A.ld + j]);
+            if (A.out) {
+                A.out[s] = (double)rho;
+                A.out[N + s] = (double)ur;
+                A.out[2 * N + s] = (double)uth;
+                A.out[3 * N + s] = (double)T;
+                A.out[4 * N + s] = lam;
             }
-        const double ux = jx / rho, uy = jy / rho;
-        double e = 0.5 * fv[0] * (ux * ux + uy * uy);
-        for (int k = 0; k < 4; ++k)
-            for (int i = 0; i < 8; ++i) {
-                const double dx = A.v[k] * cx[i] - ux, dy = A.v[k] * cy[i] - uy;
-                e += 0.5 * fv[1 + 8 * k + i] * (dx * dx + dy * dy);
-            }
-        const double T = e / rho;
-        double sth, cth;
-        sincospi(A.th_over_pi * m, &sth, &cth);
-        const double ur = ux * cth + uy * sth, uth = -ux * sth + uy * cth;
-        const double lam = LamStore<real>::to_lambda((double)A.lam[(long long)m * A.ld + j]);
-        if (A.out) {
-            A.out[s] = rho;
-            A.out[N + s] = ur;
-            A.out[2 * N + s] = uth;
-            A.out[3 * N + s] = T;
-            A.out[4 * N + s] = lam;
+            bad |= !isfinite(rho) || !isfinite(ur) || !isfinite(uth) || !isfinite(T) || !isfinite(lam);
+            const double r = A.r_in + (j + 0.5) * A.dr;  // weight r dr dtheta: dr dtheta applied per block
+            acc[0] += (double)rho * r;
+            acc[1] += (double)jx * r;
+            acc[2] += (double)jy * r;
+            acc[3] += (double)e2 * r;  // rho T + rho u^2 / 2 = (1/2) sum f v^2 for D = 2
         }
-        bad |= !isfinite(rho) || !isfinite(ur) || !isfinite(uth) || !isfinite(T) || !isfinite(lam);
-        const double w = (A.r_in + (j + 0.5) * A.dr) * A.dr * A.dtheta;
-        acc[0] += rho * w;
-        acc[1] += rho * ux * w;
-        acc[2] += rho * uy * w;
-        acc[3] += (rho * T + 0.5 * rho * (ux * ux + uy * uy)) * w;
+        const double wa = A.dr * A.dtheta;
+        acc[0] *= wa;
+        acc[1] *= wa;
+        acc[2] *= wa;
+        acc[3] *= 0.5 * wa;
+    } else {
+        double cx[8], cy[8];
+        cart_dirs(cx, cy);
+        for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+             s += (long long)gridDim.x * blockDim.x) {
+            const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
+            const real *fp = A.f + (long long)m * A.ld + j;
+            double fv[NV];
+            for (int q = 0; q < NV; ++q) fv[q] = (double)fp[(long long)q * A.plane];
+            double rho = fv[0], jx = 0.0, jy = 0.0;
+            for (int k = 0; k < 4; ++k)
+                for (int i = 0; i < 8; ++i) {
+                    const double fq = fv[1 + 8 * k + i];
+                    rho += fq;
+                    jx += fq * A.v[k] * cx[i];
+                    jy += fq * A.v[k] * cy[i];
+                }
+            const double ux = jx / rho, uy = jy / rho;
+            double e = 0.5 * fv[0] * (ux * ux + uy * uy);
+            for (int k = 0; k < 4; ++k)
+                for (int i = 0; i < 8; ++i) {
+                    const double dx = A.v[k] * cx[i] - ux, dy = A.v[k] * cy[i] - uy;
+                    e += 0.5 * fv[1 + 8 * k + i] * (dx * dx + dy * dy);
+                }
+            const double T = e / rho;
+            double sth, cth;
+            sincospi(A.th_over_pi * m, &sth, &cth);
+            const double ur = ux * cth + uy * sth, uth = -ux * sth + uy * cth;
+            const double lam = LamStore<real>::to_lambda((double)A.lam[(long long)m * A.ld + j]);
+            if (A.out) {
+                A.out[s] = rho;
+                A.out[N + s] = ur;
+                A.out[2 * N + s] = uth;
+                A.out[3 * N + s] = T;
+                A.out[4 * N + s] = lam;
+            }
+            bad |= !isfinite(rho) || !isfinite(ur) || !isfinite(uth) || !isfinite(T) || !isfinite(lam);
+            const double w = (A.r_in + (j + 0.5) * A.dr) * A.dr * A.dtheta;
+            acc[0] += rho * w;
+            acc[1] += rho * ux * w;
+            acc[2] += rho * uy * w;
+            acc[3] += (rho * T + 0.5 * rho * (ux * ux + uy * uy)) * w;
+        }
     }
     if (bad) atomicOr(A.status, ST_NONFINITE);
     // deterministic block reduction: warp shuffles, then warp 0 over the warps

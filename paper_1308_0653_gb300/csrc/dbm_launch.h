@@ -41,4 +41,8 @@ cudaError_t launch_wait_selftest(int *status, int arrive, long long limit, cudaS
 
 constexpr int MOMENT_BLOCKS = 1024;  // partial-sum slots of the totals reduction
 
+// Record a failed CUDA call as this thread's last error (dbm_last_error) and
+// return DBM_ECUDA (defined by the C-ABI runtime).
+int record_cuda_failure(cudaError_t e, const char *what);
+
 }  // namespace dbm

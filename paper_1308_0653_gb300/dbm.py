@@ -81,6 +81,8 @@ def lib():
         L.dbm_moments_device.argtypes = [H, vp, vp]
         L.dbm_steps_done.argtypes = [H]
         L.dbm_steps_done.restype = ctypes.c_int64
+        L.dbm_state_device.argtypes = [H, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64)]
+        L.dbm_totals_noalloc.argtypes = [P, vp, ctypes.c_int64, vp, vp]
         L.dbm_status.argtypes = [H, vp]
         L.dbm_export_state.argtypes = [H, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
         L.dbm_import_state.argtypes = [H, vp, vp, ctypes.c_int64, vp]
@@ -265,6 +267,22 @@ def dbm_steps_done(h) -> int:
     return int(lib().dbm_steps_done(h))
 
 
+def dbm_state_device(h):
+    """Device addresses of the current state in the handle's buffer and its
+    row stride: (f address, lambda address, ld)."""
+    f, lam, ld = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64(0)
+    _check(lib().dbm_state_device(h, ctypes.byref(f), ctypes.byref(lam), ctypes.byref(ld)),
+           "dbm_state_device")
+    return f.value, lam.value, ld.value
+
+
+def dbm_totals_noalloc(p: DbmParams, dev_f_ptr: int, ld: int, dev_totals_ptr: int, stream=None) -> int:
+    """Enqueue the allocation-free totals of f[33][ntheta][ld] at dev_f_ptr
+    into 4 device doubles at dev_totals_ptr; returns the status."""
+    return int(lib().dbm_totals_noalloc(ctypes.byref(p), ctypes.c_void_p(dev_f_ptr), int(ld),
+                                        ctypes.c_void_p(dev_totals_ptr), _stream(stream)))
+
+
 def dbm_status(h, stream=None) -> int:
     return int(lib().dbm_status(h, _stream(stream)))
 
@@ -440,6 +458,10 @@ class Simulation:
     def launch_info(self) -> dict:
         return dbm_launch_info(self.h)
 
+    def state_device(self):
+        """(f address, lambda address, ld) of the current state on the device."""
+        return dbm_state_device(self.h)
+
     def noneq(self, stream=None):
         """Delta*_m of Sec. II.E: array (12, ntheta, nr), components in NONEQ order."""
         out = np.empty((12,) + self.shape)
@@ -471,9 +493,10 @@ class Simulation:
 
     def close(self):
         if self.h is not None:
-            # steps may still be queued on any stream the caller passed, and
-            # once the buffer is dropped torch may hand it to another tensor:
-            # finish the device's work first (dbm_destroy does not wait)
+            # dbm_destroy waits for the work enqueued on the handle's buffers;
+            # work the caller queued behind it on the same streams (a copy out
+            # of the state, say) is finished too before torch may hand the
+            # buffer to another tensor
             _finish_device(self.buf)
             dbm_destroy(self.h)
             self.h = None
