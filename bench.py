@@ -88,10 +88,16 @@ def parse():
     ap.add_argument("--rows-per-item", type=int, default=0,
                     help="theta rows per work item of batches and the server (0 = library default)")
     ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--warmup-batch", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
-    ap.add_argument("--max-queue", type=int, default=1000,
+    ap.add_argument("--max-queue", type=int, default=200,
                     help="server queue bound (requests beyond it are refused and counted)")
-    ap.add_argument("--duration", type=float, default=60.0)
+    ap.add_argument("--serve-window", type=float, default=30.0,
+                    help="seconds of arrivals in each serving run")
+    ap.add_argument("--serve-drain", type=float, default=30.0,
+                    help="seconds after the window to finish the 0.7 x capacity run's requests")
+    ap.add_argument("--no-batch", action="store_true", help="default line without the batch leg")
+    ap.add_argument("--no-serve", action="store_true", help="default line without the serving leg")
     ap.add_argument("--smax", type=int, default=20000)
     ap.add_argument("--batch-nmin", type=int, default=128, help="smallest side of a batch instance")
     ap.add_argument("--batch-nmax", type=int, default=1024, help="largest side of a batch instance")
@@ -392,6 +398,15 @@ def run_ours(args):
                          "seconds": t_e2e,
                          "calls": "dbm_init_state(host) + dbm_step(K) + dbm_moments(host)"}}
 
+    # batched and served legs (one GPU: their figures are per GPU)
+    single = batch = serve = None
+    if args.gpus == 1 and not (args.no_batch and args.no_serve):
+        single = single_instance_glups(stream)
+        if not args.no_batch:
+            batch = batch_leg(args, single)
+        if not args.no_serve:
+            serve = serve_leg(args, single)
+
     cpu = None
     if rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(w, budget_s=12.0, max_rows=256)
@@ -405,7 +420,7 @@ def run_ours(args):
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": args.steps, "fp64": fp64,
                 "fp32_over_fp64": (value / args.gpus / fp64["value"]) if fp64 else None,
-                "state_finite": bool(finite)}
+                "state_finite": bool(finite), "batch": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -416,8 +431,8 @@ GRAPH_WARM = 64
 
 
 def single_instance_glups(stream, steps=500):
-    """FP32 GLUPS of one 2048^2 implosion alone (the default step-mode workload),
-    for the batched and served ratios."""
+    """FP32 GLUPS of one 2048^2 implosion alone (the default step workload),
+    measured in the same process, for the batched and served ratios."""
     import torch
     from paper_1308_0653_gb300 import dbm
     w1 = W.implosion(2048, 2048, nsteps=0)
@@ -433,12 +448,12 @@ def single_instance_glups(stream, steps=500):
     return w1.sites * NV * steps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
-def run_batch(args):
+def batch_leg(args, single):
     """64 uneven square instances (N in [128, 1024], seeded) advanced together,
-    one persistent launch per step, against the same instances run one by one."""
+    one persistent launch per step, against the same instances one by one and
+    against `single` (GLUPS of one 2048^2 instance alone)."""
     import torch
     from paper_1308_0653_gb300 import dbm
-    torch.cuda.set_device(0)
     ws = W.batch(args.instances, seed=0, nsteps=args.batch_steps, nmin=args.batch_nmin,
                  nmax=args.batch_nmax, align=1)
     sites = sum(w.sites for w in ws)
@@ -459,11 +474,11 @@ def run_batch(args):
         names = [f"v{vv}/r{rr}" for vv in (4, 2) for rr in (16, 32, 64, "scaled")]
         tune = {"variant": v, "rows_per_item": r,
                 "ms_per_step": {n: round(x, 4) for n, x in zip(names, ms) if x > 0}}
-    b.step(args.warmup, stream=stream)
+    b.step(args.warmup_batch, stream=stream)
     torch.cuda.synchronize()
     info = b.launch_info()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = args.batch_steps - args.warmup
+    steps = args.batch_steps - args.warmup_batch
     e0.record(stream)
     b.step(steps, stream=stream)
     e1.record(stream)
@@ -484,40 +499,46 @@ def run_batch(args):
     alone = sites * NV / t_one / 1e9
     for s in sims:
         s.close()
-    single = single_instance_glups(stream)
-    line = {"metric": METRIC + ", batched sweep", "value": batched, "unit": UNIT, "n_gpus": 1,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{len(ws)} instances, N x N with N uniform in "
-                                   f"[{args.batch_nmin}, {args.batch_nmax}] "
-                                   "(seed 0), explosion/implosion alternating, shock ratio "
-                                   "logU[1.2, 3], omega1 logU[0.5, 8]",
-                       "sites": sites, "launch": info, "autotune": tune},
+    return {"metric": METRIC + ", batched sweep", "value": batched, "unit": UNIT,
+            "steps": steps, "warmup": args.warmup_batch, "ms_per_step": el / steps * 1e3,
+            "workload": f"{len(ws)} instances, N x N with N uniform in [{args.batch_nmin}, "
+                        f"{args.batch_nmax}] (seed 0), explosion/implosion alternating, shock ratio "
+                        "logU[1.2, 3], omega1 logU[0.5, 8]; one persistent launch per step, CUDA "
+                        "graph of 32 steps",
+            "sites": sites, "launch": info, "autotune": tune,
             "one_by_one": {"value": alone, "unit": UNIT,
                            "how": "each instance alone, 64 graph-replayed steps, summed time"},
             "batched_over_one_by_one": batched / alone,
             "single_instance": {"value": single, "unit": UNIT,
-                                "workload": "reactive implosion 2048x2048, 500 steps"},
+                                "workload": "reactive implosion 2048x2048, 500 steps, same process"},
             "batched_over_single_instance": batched / single}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_serve(args):
-    """Poisson arrivals through dbm_submit / dbm_poll: p50/p99 time to solution
-    of completed requests and aggregate GLUPS over the run."""
+def mean_request_updates(seed=0, nmax=2048, smax=20000, n=4000):
+    """Expected site x velocity updates of one serving request (mean over the
+    first n requests of the stream's shapes)."""
+    tot = 0.0
+    for k in range(n):
+        N, steps, _, _ = W.serving_shape(k, seed=seed, nmax=nmax, smax=smax)
+        tot += N * N * NV * steps
+    return tot / n
+
+
+def serve_run(rate, duration, args, drain_s):
+    """Poisson arrivals at `rate` for `duration` s through dbm_submit /
+    dbm_poll; results are collected until every accepted request is done or
+    drain_s after the window.  Returns the run's figures."""
     import torch
     from paper_1308_0653_gb300 import dbm
-    torch.cuda.set_device(0)
     free, total = torch.cuda.mem_get_info()
     pool = int(min(free * 0.8, 150e9))
     # The server copies each request's initial fields until it is admitted, so
-    # the queue is bounded (max_queue, requests beyond it are refused with
-    # DBM_EBUSY and counted): under sustained overload an unbounded queue grows
-    # by ~30 MB of host memory per request.
+    # the queue is bounded (requests beyond it are refused with DBM_EBUSY and
+    # counted): under sustained overload an unbounded queue grows by ~30 MB of
+    # host memory per request.
     srv = dbm.Server(pool_bytes=pool, max_slots=64, max_queue=args.max_queue, quantum=64,
                      max_items=1 << 20, rows_per_item=args.rows_per_item)
-    arr = W.arrivals(args.rate, args.duration, seed=0)
+    arr = W.arrivals(rate, duration, seed=0)
     t0 = time.perf_counter()
     pending = []   # (ticket, sites): the fields are not kept here
     n_accepted = 0
@@ -530,7 +551,7 @@ def run_serve(args):
         nonlocal pending, upd
         keep = []
         for t, sites in pending:
-            st, res = srv.poll(t, timeout_us=timeout_us(t))
+            st, res = srv.poll(t, timeout_us=timeout_us())
             if st == dbm.DBM_OK:
                 if res["status"] == dbm.DBM_OK:
                     lat.append(res["t_end"] - res["t_submit"])
@@ -545,7 +566,7 @@ def run_serve(args):
         offered += w.sites * NV * w.nsteps
         while time.perf_counter() - t0 < ta:
             if time.perf_counter() - last > 0.5:
-                collect(lambda t: 0)
+                collect(lambda: 0)
                 last = time.perf_counter()
             time.sleep(0.001)
         try:
@@ -556,30 +577,66 @@ def run_serve(args):
                 raise
             refused += 1
         del w
-    # until the end of the window, then what is not done is the backlog
-    collect(lambda t: int(max(args.duration - (time.perf_counter() - t0), 0) * 1e6))
+    while time.perf_counter() - t0 < duration:
+        collect(lambda: 0)
+        time.sleep(0.05)
+    window = time.perf_counter() - t0
+    stats_w = srv.stats()
+    # then drain: what is still not done after drain_s is the backlog
+    collect(lambda: int(max(duration + drain_s - (time.perf_counter() - t0), 0) * 1e6))
     wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
-    executed_glups = stats["executed"] / wall / 1e9
-    single = single_instance_glups(torch.cuda.Stream())
     lat = np.array(lat) if lat else np.array([np.nan])
-    line = {"metric": METRIC + ", served", "value": upd / wall / 1e9, "unit": UNIT, "n_gpus": 1,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"Poisson arrivals {args.rate}/s for {args.duration} s, side "
-                                   f"logU[128, {args.nmax}], steps logU[1000, {args.smax}], "
-                                   "explosion/implosion 50/50, omega1 in {1, 2, 4}",
-                       "requests": len(arr), "accepted": n_accepted, "refused_queue_full": refused,
-                       "max_queue": args.max_queue, "pool_bytes": pool, "max_slots": 64, "quantum": 64},
-            "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.nanpercentile(lat, 50)),
-            "p99_s": float(np.nanpercentile(lat, 99)), "backlog": n_accepted - int(np.isfinite(lat).sum()),
-            "executed_glups": executed_glups,
+    done = int(np.isfinite(lat).sum())
+    return {"rate_per_s": rate, "window_s": duration, "requests": len(arr), "accepted": n_accepted,
+            "refused_queue_full": refused, "completed": done, "backlog": n_accepted - done,
+            "p50_s": float(np.nanpercentile(lat, 50)), "p99_s": float(np.nanpercentile(lat, 99)),
+            "executed_glups_window": stats_w["executed"] / window / 1e9,
+            "executed_glups": stats["executed"] / wall / 1e9,
+            "completed_glups": upd / wall / 1e9, "offered_glups": offered / duration / 1e9,
+            "wall_s": wall, "pool_bytes": pool, "server_status": stats["status"]}
+
+
+def serve_leg(args, single):
+    """Two serving runs of the config-5 request stream (side logU[128, 2048],
+    steps logU[1e3, 2e4], explosion/implosion 50/50): at its 20 req/s, which
+    overloads the GPU about five times (sustained throughput; latencies are
+    queue-dominated), then at 0.7 x the capacity that run measured
+    (time to solution)."""
+    over = serve_run(args.rate, args.serve_window, args, drain_s=0.0)
+    mean_upd = mean_request_updates(nmax=args.nmax, smax=args.smax)
+    capacity = over["executed_glups_window"] * 1e9 / mean_upd
+    light = serve_run(0.7 * capacity, args.serve_window, args, drain_s=args.serve_drain)
+    return {"metric": METRIC + ", served", "unit": UNIT,
+            "value": over["executed_glups_window"],
+            "executed_over_single_instance": over["executed_glups_window"] / single,
             "single_instance": {"value": single, "unit": UNIT,
-                                "workload": "reactive implosion 2048x2048, 500 steps"},
-            "executed_over_single_instance": executed_glups / single,
-            "offered_glups": offered / args.duration / 1e9,
-            "server": stats}
-    print(json.dumps(line), flush=True)
+                                "workload": "reactive implosion 2048x2048, 500 steps, same process"},
+            "workload": f"Poisson arrivals, side logU[128, {args.nmax}], steps logU[1000, {args.smax}], "
+                        "explosion/implosion 50/50, omega1 in {1, 2, 4}; max 64 resident, "
+                        f"queue bounded at {args.max_queue}, quantum 64 steps",
+            "mean_request_updates": mean_upd, "capacity_req_per_s": capacity,
+            "overload": over, "at_0.7_capacity": light}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    single = single_instance_glups(torch.cuda.Stream())
+    leg = batch_leg(args, single)
+    leg.update({"n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic"})
+    print(json.dumps(leg), flush=True)
+    return 0
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    single = single_instance_glups(torch.cuda.Stream())
+    leg = serve_leg(args, single)
+    leg.update({"n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic"})
+    print(json.dumps(leg), flush=True)
     return 0
 
 

@@ -69,8 +69,11 @@ extern "C" {
 /* radial boundary rules (Sec. II.D) */
 #define DBM_BC_OUTFLOW 0   /* zero-gradient ghost: f(-1) = f(0), f(nr) = f(nr-1)  */
                            /* (the paper defers annulus boundaries; reading)      */
-#define DBM_BC_CENTRE  1   /* disc centre, inner boundary only, needs r_in = 0 and */
-                           /* a sector: f(-1, theta, k, i) = f(0, theta, k, i+4)  */
+#define DBM_BC_CENTRE  1   /* disc centre, inner boundary only, needs r_in = 0.    */
+                           /* In a sector: f(-1, theta, k, i) = f(0, theta, k, i+4) */
+                           /* (the paper's rule); on a full 2 pi grid (ntheta even) */
+                           /* the point across the centre, f(-1, theta_m, k, i) =  */
+                           /* f(0, theta_{m + ntheta/2}, k, i), lambda likewise     */
 
 /* heat put into f by M (Sec. II.B) */
 #define DBM_R_EXPLICIT   0 /* R(lambda^t, P^t) of Eq. (Cochran): the paper's form */

@@ -202,8 +202,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Tensor maps of one parity's inputs: f as (ld, ntheta, 33) and lambda as
-// (ld, ntheta), box = one row of W + 2 halo columns (all 33 planes for f).
+// Tensor maps of one parity's inputs: f as (nr, ntheta, 33) and lambda as
+// (nr, ntheta) with row stride ld, box = one row of W + 2 halo columns (all
+// 33 planes for f).  The row padding [nr, ld) lies outside the maps: a box
+// that overhangs the last radial site is filled with zeros there instead of
+// reading the padding from memory (no site reads beyond nr - 1).
 template <typename real>
 bool encode_maps(const dbm_t *h, StepArgs<real> &A)
 {
@@ -213,7 +216,7 @@ bool encode_maps(const dbm_t *h, StepArgs<real> &A)
         sizeof(real) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
     const cuuint64_t e = sizeof(real);
     const cuuint32_t bx = (cuuint32_t)(h->ki.W + 2 * h->ki.halo);
-    const cuuint64_t gdim3[3] = {(cuuint64_t)h->ld, (cuuint64_t)h->p.ntheta, (cuuint64_t)NV};
+    const cuuint64_t gdim3[3] = {(cuuint64_t)h->p.nr, (cuuint64_t)h->p.ntheta, (cuuint64_t)NV};
     const cuuint64_t gstr3[2] = {(cuuint64_t)h->ld * e, (cuuint64_t)h->ld * h->p.ntheta * e};
     const cuuint32_t box3[3] = {bx, 1, (cuuint32_t)NV};
     const cuuint32_t one3[3] = {1, 1, 1};
@@ -221,7 +224,7 @@ bool encode_maps(const dbm_t *h, StepArgs<real> &A)
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    const cuuint64_t gdim2[2] = {(cuuint64_t)h->ld, (cuuint64_t)h->p.ntheta};
+    const cuuint64_t gdim2[2] = {(cuuint64_t)h->p.nr, (cuuint64_t)h->p.ntheta};
     const cuuint64_t gstr2[1] = {(cuuint64_t)h->ld * e};
     const cuuint32_t box2[2] = {bx, 1};
     return enc(&A.tm_lam, dt, 2, (void *)A.lam_in, gdim2, gstr2, box2, one3, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -255,31 +258,31 @@ void fill_step_args(dbm_t *h, StepArgs<real> (&a)[2])
         A.rows_per_item = h->rows_per_item;
         A.segs = (p.ntheta + h->rows_per_item - 1) / h->rows_per_item;
         A.items = A.strips * A.segs;
-        A.reaction_energy = p.reaction_energy;
-        A.general_pow = (p.m == 1.0 && p.n == 1.0) ? 0 : 1;
-        A.sector = p.sector;
-        A.centre = p.r_bc_inner == DBM_BC_CENTRE ? 1 : 0;
-        A.cr_scale = (real)(p.dt / dr);
-        A.ct_scale = (real)(p.dt / dth);
+        A.c.reaction_energy = p.reaction_energy;
+        A.c.general_pow = (p.m == 1.0 && p.n == 1.0) ? 0 : 1;
+        A.c.sector = p.sector;
+        A.c.centre = p.r_bc_inner == DBM_BC_CENTRE ? (p.sector ? 1 : 2) : 0;
+        A.c.cr_scale = (real)(p.dt / dr);
+        A.c.ct_scale = (real)(p.dt / dth);
         // 1 - E is taken from the rounded E (exact for E >= 1/2), so the two
         // weights of the BGK step sum to exactly 1 in `real`: independently
         // rounded they miss 1 by up to half an ulp, a relative mass error of
         // that size at every site and step with one sign, which is what
         // limits FP32 over long runs with small dt / tau
-        A.decay = (real)std::exp(-p.dt / p.tau);
-        A.one_m_decay = (real)1 - A.decay;
-        A.dt = (real)p.dt;
-        A.inv_dt = (real)(1.0 / p.dt);
-        A.Q = (real)p.Q;
-        A.omega1 = (real)p.omega1;
-        A.omega2 = (real)p.omega2;
-        A.m_exp = (real)p.m;
-        A.n_exp = (real)p.n;
-        A.T_th = (real)p.T_th;
+        A.c.decay = (real)std::exp(-p.dt / p.tau);
+        A.c.one_m_decay = (real)1 - A.c.decay;
+        A.c.dt = (real)p.dt;
+        A.c.inv_dt = (real)(1.0 / p.dt);
+        A.c.Q = (real)p.Q;
+        A.c.omega1 = (real)p.omega1;
+        A.c.omega2 = (real)p.omega2;
+        A.c.m_exp = (real)p.m;
+        A.c.n_exp = (real)p.n;
+        A.c.T_th = (real)p.T_th;
         for (int k = 0; k < 4; ++k) {
-            A.v[k] = (real)p.v[k];
-            A.v2[k] = (real)(p.v[k] * p.v[k]);
-            for (int c = 0; c < 4; ++c) A.Fc[k][c] = (real)Fc[k][c];
+            A.c.v[k] = (real)p.v[k];
+            A.c.v2[k] = (real)(p.v[k] * p.v[k]);
+            for (int c = 0; c < 4; ++c) A.c.Fc[k][c] = (real)Fc[k][c];
         }
     }
     h->tmap_ok = encode_maps(h, a[0]) && encode_maps(h, a[1]);
@@ -503,7 +506,8 @@ int dbm_check(const dbm_params *p, double *cfl)
     if (p->reserved != 0) return DBM_EINVAL;
     if (p->r_bc_outer != DBM_BC_OUTFLOW) return DBM_EINVAL;
     if (p->r_bc_inner == DBM_BC_CENTRE) {
-        if (!p->sector || p->r_in != 0.0) return DBM_EINVAL;  // the disc centre lives in a sector
+        if (p->r_in != 0.0) return DBM_EINVAL;                 // the disc centre is at r = 0
+        if (!p->sector && p->ntheta % 2 != 0) return DBM_EINVAL;  // full disc: row m + ntheta/2
     } else if (p->r_bc_inner != DBM_BC_OUTFLOW) {
         return DBM_EINVAL;
     }
@@ -1065,6 +1069,9 @@ struct dbm_batch_s {
     unsigned char *stage;     // pinned host staging of the slot and item tables
     cudaEvent_t stage_ev;
     cudaEvent_t done;         // recorded after the last batched steps enqueued
+    int cbase;                // first entry of the batch constant table held (-1: none)
+    int device;
+    unsigned char *cstage;    // pinned host staging of the slots' constants
     bool stage_pending;
     long long T;              // host mirror of the device step counter
     int n_items;
@@ -1119,11 +1126,44 @@ BatchLayout batch_layout(int max_slots, long long max_items, int precision)
     return L;
 }
 
+// Entries of the batch constant tables (one per precision), per device:
+// each batch holds a contiguous range of max_slots entries.
+std::mutex g_const_mu;
+std::map<std::pair<int, int>, std::vector<char>> g_const_used;  // (device, precision) -> used flags
+
+int const_alloc(int device, int precision, int n)
+{
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    const int cap = precision == DBM_FP64 ? batch_const_capacity<double>() : batch_const_capacity<float>();
+    std::vector<char> &used = g_const_used[{device, precision}];
+    used.resize(cap, 0);
+    for (int first = 0; first + n <= cap; ++first) {
+        int k = 0;
+        while (k < n && !used[first + k]) ++k;
+        if (k == n) {
+            std::fill(used.begin() + first, used.begin() + first + n, 1);
+            return first;
+        }
+        first += k;
+    }
+    return -1;
+}
+
+void const_free(int device, int precision, int first, int n)
+{
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    std::vector<char> &used = g_const_used[{device, precision}];
+    for (int k = first; k < first + n && k < (int)used.size(); ++k) used[k] = 0;
+}
+
 template <typename real>
 void fill_slot(dbm_batch_t *b, int s, unsigned char *dst)
 {
     BatchSlot<real> sl;
     std::memset(&sl, 0, sizeof(sl));
+    sl.cidx = b->cbase + s;
+    StepConsts<real> *cst = reinterpret_cast<StepConsts<real> *>(b->cstage) + s;
+    std::memset(cst, 0, sizeof(*cst));
     if (b->inst[s]) {
         const StepArgs<real> *a;
         if constexpr (std::is_same<real, double>::value)
@@ -1132,6 +1172,7 @@ void fill_slot(dbm_batch_t *b, int s, unsigned char *dst)
             a = b->inst[s]->a32;
         sl.args[0] = a[0];
         sl.args[1] = a[1];
+        *cst = a[0].c;
         sl.start = b->start[s];
         sl.end = b->end[s];
         sl.par0 = b->par0[s];
@@ -1339,15 +1380,27 @@ int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_p
                                   : batch_kernel_info<float>(b->variant, &b->ki);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->stage, L.items + (size_t)max_items * sizeof(int4) + 256,
                                             cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->cstage, (size_t)max_slots * sizeof(StepConsts<double>),
+                                            cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(dev_buf, 0, L.total);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
+    b->device = dev;
+    b->cbase = e == cudaSuccess ? const_alloc(dev, precision, max_slots) : -1;
+    if (e != cudaSuccess || b->cbase < 0) {
         if (b->stage) cudaFreeHost(b->stage);
+        if (b->cstage) cudaFreeHost(b->cstage);
         if (b->stage_ev) cudaEventDestroy(b->stage_ev);
         if (b->done) cudaEventDestroy(b->done);
         delete b;
+        if (e == cudaSuccess) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "dbm_batch_create: the batch constant table has no %d free entries on this device "
+                     "(%d in all for this precision, shared by the live batches)", max_slots,
+                     precision == DBM_FP64 ? batch_const_capacity<double>() : batch_const_capacity<float>());
+            return DBM_ENOMEM;
+        }
         return cuda_fail(e, "dbm_batch_create");
     }
     b->nsm = nsm;
@@ -1366,6 +1419,8 @@ int dbm_batch_destroy(dbm_batch_t *b)
     cudaEventDestroy(b->stage_ev);
     cudaEventDestroy(b->done);
     cudaFreeHost(b->stage);
+    cudaFreeHost(b->cstage);
+    const_free(b->device, b->precision, b->cbase, b->max_slots);
     delete b;
     return DBM_OK;
 }
@@ -1470,6 +1525,11 @@ int dbm_batch_commit(dbm_batch_t *b, void *stream)
     std::memcpy(b->stage + b->off_nitems, &b->n_items, sizeof(int));
     CK(cudaMemcpyAsync(b->buf + b->off_slots, b->stage, (size_t)b->max_slots * b->slot_bytes,
                        cudaMemcpyHostToDevice, st));
+    CK(b->precision == DBM_FP64
+           ? upload_batch_consts<double>(b->cbase, reinterpret_cast<const StepConsts<double> *>(b->cstage),
+                                         b->max_slots, st)
+           : upload_batch_consts<float>(b->cbase, reinterpret_cast<const StepConsts<float> *>(b->cstage),
+                                        b->max_slots, st));
     if (n > 0)
         CK(cudaMemcpyAsync(b->buf + b->off_items, b->stage + b->off_items, (size_t)n * sizeof(int4),
                            cudaMemcpyHostToDevice, st));

@@ -56,10 +56,31 @@ template <typename real> struct Halo;
 template <> struct Halo<float> { static constexpr int value = 4; };   // 16 bytes
 template <> struct Halo<double> { static constexpr int value = 2; };  // 16 bytes
 
-// Per-instance constants of the step (host-computed in double, rounded to real).
-// The tensor maps describe this parity's input f as a 3-D tensor (ld, ntheta,
-// 33) and lambda as 2-D (ld, ntheta), with a box of one row of W + 2 HALO
-// columns; they are used by the tensor-TMA variants.
+// Per-instance constants of the update (host-computed in double, rounded to
+// real).  A single-instance launch reads them from its parameter block (the
+// constant bank, as instruction operands); a batched launch reads them from
+// a constant-memory table indexed by the item's slot.
+template <typename real>
+struct StepConsts {
+    real cr_scale;        // dt / dr
+    real ct_scale;        // dt / dtheta
+    real decay;           // exp(-dt / tau)
+    real one_m_decay;     // 1 - exp(-dt / tau)
+    real dt, Q, omega1, omega2, m_exp, n_exp, T_th;
+    real inv_dt;          // 1 / dt
+    real v[4], v2[4];     // ring speeds and their squares
+    real Fc[4][4];        // F_k(T) = T (Fc[k][0] + T (Fc[k][1] + T (Fc[k][2] + T Fc[k][3])))
+    int reaction_energy;  // 0 explicit R, 1 consistent R
+    int general_pow;      // 0: m = n = 1 (P^m = P), 1: pow()
+    int sector;           // 1: pi/4 sector, theta wrap rotates velocities by one direction
+    int centre;           // disc centre at r = 0: 1 in a sector (ghost j = -1 is j = 0 with
+                          // i -> i+4), 2 on a full grid (ghost is j = 0 of row m + ntheta/2)
+};
+
+// Step arguments of one instance and one ping-pong parity.  The tensor maps
+// describe this parity's input f as a 3-D tensor (ld, ntheta, 33) and lambda
+// as 2-D (ld, ntheta), with a box of one row of W + 2 HALO columns; they are
+// used by the tensor-TMA variants.
 template <typename real>
 struct StepArgs {
     CUtensorMap tm_f;     // 128 B, 64-byte aligned
@@ -77,19 +98,12 @@ struct StepArgs {
     int rows_per_item;    // theta rows per work item
     int segs;             // ceil(ntheta / rows_per_item)
     int items;            // strips * segs
-    int reaction_energy;  // 0 explicit R, 1 consistent R
-    int general_pow;      // 0: m = n = 1 (P^m = P), 1: pow()
-    int sector;           // 1: pi/4 sector, theta wrap rotates velocities by one direction
-    int centre;           // 1: disc centre at r = 0 (ghost j = -1 is j = 0 with i -> i+4)
-    real cr_scale;        // dt / dr
-    real ct_scale;        // dt / dtheta
-    real decay;           // exp(-dt / tau)
-    real one_m_decay;     // 1 - exp(-dt / tau)
-    real dt, Q, omega1, omega2, m_exp, n_exp, T_th;
-    real inv_dt;          // 1 / dt
-    real v[4], v2[4];     // ring speeds and their squares
-    real Fc[4][4];        // F_k(T) = T (Fc[k][0] + T (Fc[k][1] + T (Fc[k][2] + T Fc[k][3])))
+    StepConsts<real> c;
 };
+
+// Constant-memory table of the batched launches' per-slot constants (one
+// per precision translation unit, defined there).
+template <typename real> __device__ const StepConsts<real> &batch_consts(int i);
 
 // ---------------------------------------------------------------------------
 // PTX helpers (mbarrier + TMA bulk copy)
@@ -350,8 +364,9 @@ __device__ __forceinline__ void ring_moments(const real (&f)[NV], const real (&v
 // moments and equilibrium use the fixed direction cosines; its polar Courant
 // numbers use the row's c_i = cos(i pi/4 - theta_m), s_i = sin(...).
 // ---------------------------------------------------------------------------
-template <typename real, int WP, bool REREAD = false, int LAMOFF = NV * WP>
-__device__ __forceinline__ void site_update(const StepArgs<real> &A, const real *__restrict__ sp,
+template <typename real, int WP, bool REREAD = false, int LAMOFF = NV * WP, bool DIR_OUTER = false>
+__device__ __forceinline__ void site_update(const StepArgs<real> &A, const StepConsts<real> &C,
+                                            const real *__restrict__ sp,
                                             const real *__restrict__ sc,
                                             const real *__restrict__ sn, int col, int j, int m,
                                             real inv_r, const real (&cs)[8], const real (&sn8)[8])
@@ -373,7 +388,7 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     // --- a2: moments, ring by ring (Cartesian components) ------------------
     //     rho = sum f, rho u = sum f v, e2 = sum f v^2, T = (e2/rho - u^2)/2
     real rho, jx, jy, e2;
-    ring_moments<real>(f, A.v, A.v2, rho, jx, jy, e2);
+    ring_moments<real>(f, C.v, C.v2, rho, jx, jy, e2);
     const real inv_rho = O::rcp(rho);
     const real ux = O::mul(jx, inv_rho), uy = O::mul(jy, inv_rho);
     const real u2 = O::fma(ux, ux, O::mul(uy, uy));
@@ -385,7 +400,7 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     real Fsum = real(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        F[k] = O::mul(T, O::fma(T, O::fma(T, O::fma(T, A.Fc[k][3], A.Fc[k][2]), A.Fc[k][1]), A.Fc[k][0]));
+        F[k] = O::mul(T, O::fma(T, O::fma(T, O::fma(T, C.Fc[k][3], C.Fc[k][2]), C.Fc[k][1]), C.Fc[k][0]));
         Fsum = O::add(Fsum, F[k]);
     }
     const real F0 = O::fma(real(-8), Fsum, one);
@@ -410,13 +425,13 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     // --- a5: Cochran rate with ignition gate; exact lambda step (a9) -------
     const real P = O::mul(rho, T);
     real a = real(0), b = real(0);
-    if (T > A.T_th) {
-        if (A.general_pow) {
-            a = O::mul(A.omega1, pow_(P, A.m_exp));
-            b = O::mul(A.omega2, pow_(P, A.n_exp));
+    if (T > C.T_th) {
+        if (C.general_pow) {
+            a = O::mul(C.omega1, pow_(P, C.m_exp));
+            b = O::mul(C.omega2, pow_(P, C.n_exp));
         } else {
-            a = O::mul(A.omega1, P);
-            b = O::mul(A.omega2, P);
+            a = O::mul(C.omega1, P);
+            b = O::mul(C.omega2, P);
         }
     }
     const real om = kY ? lst : O::sub(one, lam);  // 1 - lambda
@@ -426,95 +441,163 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     real dlam = real(0);
     if (sab > real(0)) {
         // lam+ - lam = (1-lam)(a+b lam)(E-1) / [(a+b) + (a+b lam)(E-1)], E = e^{(a+b)dt}
-        const real em1 = expm1_(O::mul(sab, A.dt));
+        const real em1 = expm1_(O::mul(sab, C.dt));
         dlam = O::mul(O::mul(O::mul(om, g), em1), O::rcp(O::fma(g, em1, sab)));
     }
-    if (A.reaction_energy) R = O::mul(dlam, A.inv_dt);
+    if (C.reaction_energy) R = O::mul(dlam, C.inv_dt);
 
     // --- a6+a7 coefficients: f_new = poly(xi) (beta_k - gamma_k xi) + ... ---
     //     M = f^eq ((v-u)^2 - 2T) / (2T^2) Q R with (v-u)^2 = v_k^2 + u^2 - 2 T xi
-    const real dtQR = O::mul(A.dt, O::mul(A.Q, R));
+    const real dtQR = O::mul(C.dt, O::mul(C.Q, R));
     const real half_inv_T2 = O::mul(O::mul(half, inv_T), inv_T);
     const real gam = O::mul(dtQR, inv_T);
     const real u2m2T = O::fma(real(-2), T, u2);
-    const real beta0 = O::mul(O::mul(rho, F0), O::fma(O::mul(dtQR, u2m2T), half_inv_T2, A.one_m_decay));
+    const real beta0 = O::mul(O::mul(rho, F0), O::fma(O::mul(dtQR, u2m2T), half_inv_T2, C.one_m_decay));
 
     // --- a8: per-direction Courant magnitudes and upwind neighbours --------
-    real ar[8], at[8], sa[8];
-    int rn[8], tn[8];
     const int to_prev = (int)(sp - sc), to_next = (int)(sn - sc);
-    const bool wrap_prev = A.sector && m == 0;             // row -1 = last row, i -> i+1
-    const bool wrap_next = A.sector && m == A.ntheta - 1;  // row ntheta = row 0, i -> i-1
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        ar[i] = O::mul(fabs(cs[i]), A.cr_scale);
-        at[i] = O::mul(O::mul(fabs(sn8[i]), A.ct_scale), inv_r);
-        sa[i] = O::add(ar[i], at[i]);
+    const bool wrap_prev = C.sector && m == 0;             // row -1 = last row, i -> i+1
+    const bool wrap_next = C.sector && m == A.ntheta - 1;  // row ntheta = row 0, i -> i-1
+    // direction i: |C_r| / v_k, |C_theta| / v_k, their sum, and the shared-memory
+    // offsets of the upwind neighbours in r and theta (false: a debug check failed)
+    auto geom = [&](int i, real &ar, real &at, real &sa, int &rn, int &tn) -> bool {
+        ar = O::mul(fabs(cs[i]), C.cr_scale);
+        at = O::mul(O::mul(fabs(sn8[i]), C.ct_scale), inv_r);
+        sa = O::add(ar, at);
         int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
         if (j == 0 && o < 0) {
-            // inner ghost: zero-gradient, or the disc centre (same site, i -> i+4)
-            o = A.centre ? (((i + 4) & 7) - i) * WP : 0;
+            // inner ghost: zero-gradient; the disc centre in a sector (same
+            // site, i -> i+4); on a full disc the site across the centre,
+            // which fill_centre_ghost put in the halo column before col
+            o = C.centre == 1 ? (((i + 4) & 7) - i) * WP : (C.centre == 2 ? -1 : 0);
         } else if (j == A.nr - 1 && o > 0) {
             o = 0;  // zero-gradient outer ghost
         }
-        rn[i] = col + o;
+        rn = col + o;
         if (sn8[i] >= real(0))  // C_theta >= 0: row m-1
-            tn[i] = col + to_prev + (wrap_prev ? (((i + 1) & 7) - i) * WP : 0);
+            tn = col + to_prev + (wrap_prev ? (((i + 1) & 7) - i) * WP : 0);
         else
-            tn[i] = col + to_next + (wrap_next ? (((i + 7) & 7) - i) * WP : 0);
+            tn = col + to_next + (wrap_next ? (((i + 7) & 7) - i) * WP : 0);
 #ifdef DBM_DEBUG
-        {
-            // velocity planes q = 1 + i .. 25 + i of direction i: neighbour
-            // reads stay inside the 33 planes of their row buffer
-            const int tr = tn[i] - (sn8[i] >= real(0) ? to_prev : to_next);
-            const bool ok = (1 + i) * WP + rn[i] >= 0 && (25 + i) * WP + rn[i] < NV * WP &&
-                            (1 + i) * WP + tr >= 0 && (25 + i) * WP + tr < NV * WP;
-            if (!DBM_DEBUG_CHECK(ok, A.status)) return;
-        }
+        // velocity planes q = 1 + i .. 25 + i of direction i: neighbour
+        // reads stay inside the 33 planes of their row buffer
+        const int tr = tn - (sn8[i] >= real(0) ? to_prev : to_next);
+        const bool ok = (1 + i) * WP + rn >= 0 && (25 + i) * WP + rn < NV * WP &&
+                        (1 + i) * WP + tr >= 0 && (25 + i) * WP + tr < NV * WP;
+        return DBM_DEBUG_CHECK(ok, A.status);
+#else
+        return true;
 #endif
-    }
+    };
 
     // --- a7 + a11: update all velocities and store ------------------------
     //     f_new = f^eq (1 - E + dt M/f^eq) + (E - |C_r| - |C_th|) f
     //             + |C_r| f(upwind r) + |C_th| f(upwind theta)
+    //     with f^eq (1 - E + dt M / f^eq) = poly(xi) (beta_k - gamma_k xi) in ring k
     real *out = A.f_out + (long long)m * A.ld + j;
-    out[0] = O::fma(A0, beta0, O::mul(A.decay, REREAD ? sc[col] : f[0]));
+    out[0] = O::fma(A0, beta0, O::mul(C.decay, REREAD ? sc[col] : f[0]));
+    if constexpr (sizeof(real) == 8 || !DIR_OUTER) {
+        // Ring by ring with the geometry of all 8 directions held: the
+        // single-instance kernels and FP64.
+        real ar[8], at[8], sa[8];
+        int rn[8], tn[8];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const real vk = A.v[k];
-        const real rF = O::mul(rho, F[k]);
-        const real beta = O::mul(rF, O::fma(O::mul(dtQR, O::add(A.v2[k], u2m2T)), half_inv_T2, A.one_m_decay));
-        const real gamma = O::mul(rF, gam);
-        // one velocity given its xi and the equilibrium polynomial at xi
-        auto update_one = [&](int i, real xi, real poly) {
-            const int q = 1 + 8 * k + i;
-            real t = O::mul(poly, O::fma(-gamma, xi, beta));
-            // REREAD: take f from shared memory again instead of holding all
-            // 33 values in registers across the moment pass (fewer registers)
-            const real fq = REREAD ? sc[q * WP + col] : f[q];
-            t = O::fma(O::fma(-vk, sa[i], A.decay), fq, t);
-            const real adv = O::fma(ar[i], sc[q * WP + rn[i]], O::mul(at[i], sc[q * WP + tn[i]]));
-            t = O::fma(vk, adv, t);
-            out[(long long)q * A.plane] = t;
-        };
-        if constexpr (sizeof(real) == 8) {
-            // FP64 is bound by its arithmetic: opposite directions i and i+4
-            // have xi and -xi, so the polynomial splits into an even part E
-            // and an odd part O evaluated once, poly(+-xi) = E +- O
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const real xi = O::mul(vk, w[i]);
-                const real x2 = O::mul(xi, xi);
-                const real Ev = O::fma(x2, O::fma(x2, real(1.0 / 24.0), A2), A0);
-                const real Od = O::mul(xi, O::fma(x2, real(1.0 / 6.0), A1));
-                update_one(i, xi, O::add(Ev, Od));
-                update_one(i + 4, -xi, O::sub(Ev, Od));
+        for (int i = 0; i < 8; ++i) {
+            // as geom(i, ...), written out: the compiler schedules this form better
+            ar[i] = O::mul(fabs(cs[i]), C.cr_scale);
+            at[i] = O::mul(O::mul(fabs(sn8[i]), C.ct_scale), inv_r);
+            sa[i] = O::add(ar[i], at[i]);
+            int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
+            if (j == 0 && o < 0) {
+                o = C.centre == 1 ? (((i + 4) & 7) - i) * WP : (C.centre == 2 ? -1 : 0);
+            } else if (j == A.nr - 1 && o > 0) {
+                o = 0;  // zero-gradient outer ghost
             }
-        } else {
+            rn[i] = col + o;
+            if (sn8[i] >= real(0))  // C_theta >= 0: row m-1
+                tn[i] = col + to_prev + (wrap_prev ? (((i + 1) & 7) - i) * WP : 0);
+            else
+                tn[i] = col + to_next + (wrap_next ? (((i + 7) & 7) - i) * WP : 0);
+#ifdef DBM_DEBUG
+            {
+                // velocity planes q = 1 + i .. 25 + i of direction i: neighbour
+                // reads stay inside the 33 planes of their row buffer
+                const int tr = tn[i] - (sn8[i] >= real(0) ? to_prev : to_next);
+                const bool ok = (1 + i) * WP + rn[i] >= 0 && (25 + i) * WP + rn[i] < NV * WP &&
+                                (1 + i) * WP + tr >= 0 && (25 + i) * WP + tr < NV * WP;
+                if (!DBM_DEBUG_CHECK(ok, A.status)) return;
+            }
+#endif
+        }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            const real vk = C.v[k];
+            const real rF = O::mul(rho, F[k]);
+            const real beta = O::mul(rF, O::fma(O::mul(dtQR, O::add(C.v2[k], u2m2T)), half_inv_T2, C.one_m_decay));
+            const real gamma = O::mul(rF, gam);
+            // one velocity given its xi and the equilibrium polynomial at xi
+            auto update_one = [&](int i, real xi, real poly) {
+                const int q = 1 + 8 * k + i;
+                real t = O::mul(poly, O::fma(-gamma, xi, beta));
+                // REREAD: take f from shared memory again instead of holding all
+                // 33 values in registers across the moment pass (fewer registers)
+                const real fq = REREAD ? sc[q * WP + col] : f[q];
+                t = O::fma(O::fma(-vk, sa[i], C.decay), fq, t);
+                const real adv = O::fma(ar[i], sc[q * WP + rn[i]], O::mul(at[i], sc[q * WP + tn[i]]));
+                t = O::fma(vk, adv, t);
+                out[(long long)q * A.plane] = t;
+            };
+            if constexpr (sizeof(real) == 8) {
+                // FP64 is bound by its arithmetic: opposite directions i and
+                // i+4 have xi and -xi, so the polynomial splits into an even
+                // part E and an odd part O evaluated once, poly(+-xi) = E +- O
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const real xi = O::mul(vk, w[i]);
+                    const real x2 = O::mul(xi, xi);
+                    const real Ev = O::fma(x2, O::fma(x2, real(1.0 / 24.0), A2), A0);
+                    const real Od = O::mul(xi, O::fma(x2, real(1.0 / 6.0), A1));
+                    update_one(i, xi, O::add(Ev, Od));
+                    update_one(i + 4, -xi, O::sub(Ev, Od));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const real xi = O::mul(vk, w[i]);
+                    update_one(i, xi, O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0));
+                }
+            }
+        }
+    } else {
+        // FP32 with DIR_OUTER (batched launches, which hold each instance's
+        // constants in registers): direction by direction, so that only one
+        // direction's geometry is live at a time.  Each velocity's arithmetic
+        // is the ring-by-ring one, operation for operation: same bits.
+        real beta[4], gamma[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const real rF = O::mul(rho, F[k]);
+            beta[k] = O::mul(rF, O::fma(O::mul(dtQR, O::add(C.v2[k], u2m2T)), half_inv_T2, C.one_m_decay));
+            gamma[k] = O::mul(rF, gam);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            real ar, at, sa;
+            int rn, tn;
+            if (!geom(i, ar, at, sa, rn, tn)) return;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = 1 + 8 * k + i;
+                const real vk = C.v[k];
                 const real xi = O::mul(vk, w[i]);
-                update_one(i, xi, O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0));
+                const real poly =
+                    O::fma(xi, O::fma(xi, O::fma(xi, O::fma(xi, real(1.0 / 24.0), real(1.0 / 6.0)), A2), A1), A0);
+                real t = O::mul(poly, O::fma(-gamma[k], xi, beta[k]));
+                const real fq = REREAD ? sc[q * WP + col] : f[q];
+                t = O::fma(O::fma(-vk, sa, C.decay), fq, t);
+                const real adv = O::fma(ar, sc[q * WP + rn], O::mul(at, sc[q * WP + tn]));
+                t = O::fma(vk, adv, t);
+                out[(long long)q * A.plane] = t;
             }
         }
     }
@@ -524,14 +607,14 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
     const real ur = O::fma(ux, cth, O::mul(uy, sth));
     const real uth = O::fma(uy, cth, -O::mul(ux, sth));
     int orr = ur >= real(0) ? -1 : 1;
-    if ((j == 0 && orr < 0) || (j == A.nr - 1 && orr > 0)) orr = 0;
+    if ((j == 0 && orr < 0 && C.centre != 2) || (j == A.nr - 1 && orr > 0)) orr = 0;
     // transport acts on the stored variable alike (y - y_nb = lambda_nb - lambda);
     // the reaction step adds dlam to lambda, so it is taken off y
     if (!DBM_DEBUG_CHECK(col + orr >= 0 && col + orr < WP, A.status)) return;
     const real lr = sc[LAMOFF + col + orr];
     const real lt = (uth >= real(0) ? sp : sn)[LAMOFF + col];
-    const real tr = O::mul(O::mul(fabs(ur), A.cr_scale), O::sub(lst, lr));
-    const real tt = O::mul(O::mul(O::mul(fabs(uth), A.ct_scale), inv_r), O::sub(lst, lt));
+    const real tr = O::mul(O::mul(fabs(ur), C.cr_scale), O::sub(lst, lr));
+    const real tt = O::mul(O::mul(O::mul(fabs(uth), C.ct_scale), inv_r), O::sub(lst, lt));
     real ln;
     if constexpr (sizeof(real) == 4) {
         // y - dlam - tr - tt summed exactly, then rounded without bias
@@ -554,6 +637,30 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const real 
 }
 
 // ---------------------------------------------------------------------------
+// Full disc (centre == 2, Sec. II.D with a full 2 pi grid): the inner ghost of
+// radial site 0 in row m is site 0 of row m + ntheta/2, the point across the
+// centre, with the same (Cartesian) velocity and the same lambda.  The thread
+// of site 0 copies those 33 f and lambda from the step's input into the halo
+// column HALO - 1 of its own row buffer, where its backward differences read
+// them; no other thread reads that column of the row.  The caller fences the
+// generic writes against the TMA copies that later refill the buffer.
+// ---------------------------------------------------------------------------
+template <typename real, int WP, int LAMOFF, int HALO>
+__device__ __forceinline__ void fill_centre_ghost(const StepArgs<real> &A, real *sc, int m)
+{
+    const int half = A.ntheta / 2;
+    const int mm = m + half < A.ntheta ? m + half : m + half - A.ntheta;
+    const real *src = A.f_in + (long long)mm * A.ld;
+    real g[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) g[q] = src[(long long)q * A.plane];
+    const real lg = A.lam_in[(long long)mm * A.ld];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sc[q * WP + HALO - 1] = g[q];
+    sc[LAMOFF + HALO - 1] = lg;
+}
+
+// ---------------------------------------------------------------------------
 // Work lists.  A work item is W radial sites x a run of theta rows of one
 // instance.  SingleWork decodes items of one instance arithmetically (its
 // arguments live in kernel parameter space); BatchWork reads items of many
@@ -566,9 +673,10 @@ struct SingleWork {
     const StepArgs<real> *A;
     __device__ __forceinline__ int count() const { return A->items; }
     __device__ __forceinline__ bool item(int it, const StepArgs<real> *&a, int &j0, int &mb,
-                                         int &me) const
+                                         int &me, int &cidx) const
     {
         a = A;
+        cidx = -1;
         const int strip = it % A->strips;
         const int seg = it / A->strips;
         j0 = strip * W;
@@ -585,7 +693,7 @@ struct BatchSlot {
     StepArgs<real> args[2];  // [p]: reads buffer p, writes buffer 1 - p
     long long start, end;
     int par0;                // the instance's buffer index at global step start
-    int pad;
+    int cidx;                // the instance's entry in the batch constant table
 };
 
 template <typename real>
@@ -606,13 +714,14 @@ struct BatchWork {
     long long T;
     __device__ __forceinline__ int count() const { return n; }
     __device__ __forceinline__ bool item(int it, const StepArgs<real> *&a, int &j0, int &mb,
-                                         int &me) const
+                                         int &me, int &cidx) const
     {
         const int4 e = items[it];
         if (e.x < 0) return false;  // padding of the load-balanced table
         const BatchSlot<real> &sl = slots[e.x];
         if (T < sl.start || T >= sl.end) return false;
         a = &sl.args[(int)((T - sl.start + sl.par0) & 1)];
+        cidx = sl.cidx;
         j0 = e.y;
         mb = e.z;
         me = e.w;
@@ -654,20 +763,20 @@ __device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
     long long total_loads = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const StepArgs<real> *a;
-        int j0, mb, me;
-        if (work.item(it, a, j0, mb, me)) total_loads += (me - mb) + 2;
+        int j0, mb, me, cidx;
+        if (work.item(it, a, j0, mb, me, cidx)) total_loads += (me - mb) + 2;
     }
 
     // Producer cursor (replicated in the lanes of warp 0).
     long long issued = 0;
     int p_item = blockIdx.x, p_row = 0;
     const StepArgs<real> *pa = nullptr;
-    int pj0 = 0, pmb = 0, pme = 0;
+    int pj0 = 0, pmb = 0, pme = 0, pcidx = 0;
     bool p_ok = false;
 
     auto issue_one = [&]() {
         while (!p_ok) {  // find the next active item
-            p_ok = work.item(p_item, pa, pj0, pmb, pme);
+            p_ok = work.item(p_item, pa, pj0, pmb, pme, pcidx);
             if (!p_ok) p_item += gridDim.x;
         }
         int m = pmb - 1 + p_row;
@@ -675,7 +784,7 @@ __device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
         m = m < 0 ? m + nth : (m >= nth ? m - nth : m);
         const int slot = (int)(issued % NSTAGE);
         const int jlo = max(pj0 - HALO, 0);
-        const int jhi = min(pj0 + W + HALO, pa->ld);
+        const int jhi = min(pj0 + W + HALO, (pa->nr + HALO - 1) / HALO * HALO);  // row padding not read
         const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
         real *dst = sm + slot * SLOT + (jlo - (pj0 - HALO));
         if (lane == 0) mbar_arrive_expect_tx(&bars[slot], nbytes * NARR);
@@ -701,8 +810,8 @@ __device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
     bool ok = true;
     for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         const StepArgs<real> *ga;
-        int j0, mb, me;
-        if (!work.item(it, ga, j0, mb, me)) continue;
+        int j0, mb, me, cidx;
+        if (!work.item(it, ga, j0, mb, me, cidx)) continue;
         const StepArgs<real> *ap = ga;
         if constexpr (Work::kCopyArgs) {
             // per-instance constants into shared memory (read by every thread)
@@ -713,6 +822,7 @@ __device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
             ap = sargs;
         }
         const StepArgs<real> &A = *ap;
+        const StepConsts<real> &C = Work::kCopyArgs ? batch_consts<real>(cidx) : A.c;
         const int L = me - mb;
         const int j = j0 + tx;
         const bool active = j < A.nr;
@@ -738,8 +848,11 @@ __device__ __forceinline__ void march(const Work &work, unsigned char *smem_raw,
                     cs[i] = rt[i];
                     sn8[i] = rt[8 + i];
                 }
-                site_update<real, WP>(A, sm + ((P - 1) % NSTAGE) * SLOT, sm + (P % NSTAGE) * SLOT,
+                const bool ghost = C.centre == 2 && j == 0;
+                if (ghost) fill_centre_ghost<real, WP, NV * WP, HALO>(A, sm + (P % NSTAGE) * SLOT, m);
+                site_update<real, WP>(A, C, sm + ((P - 1) % NSTAGE) * SLOT, sm + (P % NSTAGE) * SLOT,
                                       sm + ((P + 1) % NSTAGE) * SLOT, HALO + tx, j, m, inv_r, cs, sn8);
+                if (ghost) fence_proxy_async_smem();
             }
             __syncthreads();
             if (abort_flag) {
@@ -849,9 +962,9 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
     if ((smem_addr(smem_raw) & 127u) != 0u) {  // layout assumption broken: report, copy nothing
         if (tx == 0 && nitems > 0) {
             const StepArgs<real> *a;
-            int j0, mb, me;
+            int j0, mb, me, cidx;
             for (int it = blockIdx.x; it < nitems; it += gridDim.x)
-                if (work.item(it, a, j0, mb, me)) {
+                if (work.item(it, a, j0, mb, me, cidx)) {
                     atomicOr(a->status, ST_SMEM_ALIGN);
                     break;
                 }
@@ -864,18 +977,18 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         int total_loads = 0;  // ring positions of this CTA (32-bit: cheap slot arithmetic)
         for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
             const StepArgs<real> *a;
-            int j0, mb, me;
-            if (work.item(it, a, j0, mb, me)) total_loads += (me - mb) + 2;
+            int j0, mb, me, cidx;
+            if (work.item(it, a, j0, mb, me, cidx)) total_loads += (me - mb) + 2;
         }
         int issued = 0;
         int p_item = blockIdx.x, p_row = 0;
         const StepArgs<real> *pa = nullptr;
-        int pj0 = 0, pmb = 0, pme = 0;
+        int pj0 = 0, pmb = 0, pme = 0, pcidx = 0;
         bool p_ok = false;
         while (issued < total_loads) {
             const int slot = issued % NSTAGE;
             while (!p_ok) {
-                p_ok = work.item(p_item, pa, pj0, pmb, pme);
+                p_ok = work.item(p_item, pa, pj0, pmb, pme, pcidx);
                 if (!p_ok) p_item += gridDim.x;
             }
             if (issued >= NSTAGE) {
@@ -896,7 +1009,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 // the row is in the grid; the strip starts inside the row; a tensor
                 // box's first column is on a 16-byte boundary; bulk extents are
                 // inside the padded row and multiples of 16 bytes
-                const int jlo = max(pj0 - HALO, 0), jhi = min(pj0 + W + HALO, pa->ld);
+                const int jlo = max(pj0 - HALO, 0), jhi = min(pj0 + W + HALO, (pa->nr + HALO - 1) / HALO * HALO);
                 bool ok = m >= 0 && m < nth && pj0 >= 0 && pj0 < pa->nr && pa->nr <= pa->ld;
                 if (TMAP) ok = ok && ((pj0 - HALO) * (int)sizeof(real)) % 16 == 0;
                 else ok = ok && jhi > jlo && ((jhi - jlo) * (int)sizeof(real)) % 16 == 0 &&
@@ -928,7 +1041,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                 __syncwarp();
             } else {
                 const int jlo = max(pj0 - HALO, 0);
-                const int jhi = min(pj0 + W + HALO, pa->ld);
+                const int jhi = min(pj0 + W + HALO, (pa->nr + HALO - 1) / HALO * HALO);  // row padding not read
                 const uint32_t nbytes = (uint32_t)((jhi - jlo) * (int)sizeof(real));
                 real *dst = buf + (jlo - (pj0 - HALO));
                 if (lane == 0) mbar_arrive_expect_tx(&full[slot], nbytes * NARR + TAB * (uint32_t)sizeof(real));
@@ -955,7 +1068,7 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         int parity = 0;
         bool ok = true;
         // One work item: rows [mb, me) of the strip starting at radial site j0.
-        auto run_item = [&](const StepArgs<real> &A, int j0, int mb, int me) {
+        auto run_item = [&](const StepArgs<real> &A, const StepConsts<real> &C, int j0, int mb, int me) {
             const int L = me - mb;
             const int j = j0 + tx;
             const bool active = j < A.nr;
@@ -981,9 +1094,13 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                         cs[i] = rt[i];
                         sn8[i] = rt[8 + i];
                     }
-                    site_update<real, WP, REREAD, LAMOFF>(A, sm + ((P - 1) % NSTAGE) * SLOT, sc,
+                    const bool ghost = C.centre == 2 && j == 0;
+                    if (ghost)
+                        fill_centre_ghost<real, WP, LAMOFF, HALO>(A, sm + (P % NSTAGE) * SLOT, mb + c - 1);
+                    site_update<real, WP, REREAD, LAMOFF, Work::kCopyArgs>(A, C, sm + ((P - 1) % NSTAGE) * SLOT, sc,
                                                   sm + ((P + 1) % NSTAGE) * SLOT, HALO + tx, j,
                                                   mb + c - 1, inv_r, cs, sn8);
+                    if (ghost) fence_proxy_async_smem();
                 }
                 __syncwarp();
                 if (lane == 0) {
@@ -998,8 +1115,8 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
         };
         for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
             const StepArgs<real> *ga;
-            int j0, mb, me;
-            if (!work.item(it, ga, j0, mb, me)) continue;
+            int j0, mb, me, cidx;
+            if (!work.item(it, ga, j0, mb, me, cidx)) continue;
             if constexpr (Work::kCopyArgs) {
                 // per-instance constants into shared memory, double-buffered:
                 // the barrier of the previous item guarantees nobody still
@@ -1010,19 +1127,24 @@ __device__ __forceinline__ void march2(const Work &work, unsigned char *smem_raw
                     reinterpret_cast<int *>(dst)[q] = reinterpret_cast<const int *>(ga)[q];
                 named_bar_sync(1, W);
                 parity ^= 1;
-                // and (FP32) from there into registers for the item: the update
-                // reads about 40 of them per site, which a single instance takes
-                // from the constant bank as instruction operands.  FP64 is bound
-                // by its arithmetic pipe and short of registers: it reads them
-                // from shared memory.
+                // FP32: the item's pointers and sizes from there, and its
+                // constants from the batch constant table, into registers for
+                // the item (a single instance reads its constants from the
+                // constant bank as instruction operands).  The table is
+                // constant memory, so where registers run short the compiler
+                // can load a constant again instead of spilling it.  FP64 is
+                // bound by its arithmetic pipe and short of registers: it
+                // reads them where they are.
+                const StepConsts<real> &C = batch_consts<real>(cidx);
                 if constexpr (sizeof(real) == 4) {
                     const StepArgs<real> Areg = *dst;
-                    run_item(Areg, j0, mb, me);
+                    const StepConsts<real> Creg = C;
+                    run_item(Areg, Creg, j0, mb, me);
                 } else {
-                    run_item(*dst, j0, mb, me);
+                    run_item(*dst, C, j0, mb, me);
                 }
             } else {
-                run_item(*ga, j0, mb, me);
+                run_item(*ga, ga->c, j0, mb, me);
             }
         }
     }

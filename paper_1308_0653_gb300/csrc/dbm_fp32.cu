@@ -10,6 +10,7 @@
     X(4, 3, 128, 6, false, 2) X(5, 3, 128, 4, true, 3)
 #define DBM_DEFAULT_VARIANT 4
 #define DBM_FALLBACK_VARIANT 2
+#define DBM_BATCH_CONST_SLOTS 256  // batch constant table entries (160 B each)
 #include "dbm_launch_impl.cuh"
 
 namespace dbm {

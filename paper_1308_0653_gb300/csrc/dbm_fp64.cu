@@ -9,4 +9,5 @@
     X(4, 3, 64, 5, false, 2) X(5, 3, 64, 4, true, 3)
 #define DBM_DEFAULT_VARIANT 2
 #define DBM_FALLBACK_VARIANT 2
+#define DBM_BATCH_CONST_SLOTS 128  // batch constant table entries (304 B each)
 #include "dbm_launch_impl.cuh"

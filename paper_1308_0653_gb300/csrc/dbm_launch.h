@@ -32,6 +32,11 @@ template <typename real> cudaError_t batch_kernel_info(int variant, KernelInfo *
 template <typename real>
 cudaError_t launch_batch_step(int variant, const BatchArgs<real> &B, int grid, cudaStream_t s);
 cudaError_t launch_batch_advance(long long *T, int k, cudaStream_t s);
+// Entries of the batch constant table of a precision, and a stream-ordered
+// write of n entries from host memory (pinned for an asynchronous copy).
+template <typename real> int batch_const_capacity();
+template <typename real>
+cudaError_t upload_batch_consts(int first, const StepConsts<real> *src, int n, cudaStream_t s);
 template <typename real> cudaError_t launch_init(const InitArgs<real> &A, cudaStream_t s);
 template <typename real> cudaError_t launch_moments(const MomArgs<real> &A, int grid, cudaStream_t s);
 template <typename real> cudaError_t launch_noneq(const MomArgs<real> &A, int grid, cudaStream_t s);

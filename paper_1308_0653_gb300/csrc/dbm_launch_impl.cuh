@@ -8,6 +8,28 @@
 
 namespace dbm {
 
+// Per-slot constants of the batched launches of this precision: entries are
+// handed out to batches in contiguous ranges by the runtime and written with
+// stream-ordered copies when a batch commits its slot table.
+__constant__ StepConsts<DBM_REAL> c_batch_consts[DBM_BATCH_CONST_SLOTS];
+
+template <>
+__device__ __forceinline__ const StepConsts<DBM_REAL> &batch_consts<DBM_REAL>(int i)
+{
+    return c_batch_consts[i];
+}
+
+template <> int batch_const_capacity<DBM_REAL>() { return DBM_BATCH_CONST_SLOTS; }
+
+template <>
+cudaError_t upload_batch_consts<DBM_REAL>(int first, const StepConsts<DBM_REAL> *src, int n, cudaStream_t s)
+{
+    if (first < 0 || n < 0 || first + n > DBM_BATCH_CONST_SLOTS) return cudaErrorInvalidValue;
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyToSymbolAsync(c_batch_consts, src, sizeof(StepConsts<DBM_REAL>) * (size_t)n,
+                                   sizeof(StepConsts<DBM_REAL>) * (size_t)first, cudaMemcpyHostToDevice, s);
+}
+
 namespace {
 
 template <int VER, int W, int NS, bool RR, int MB> struct Variant;
@@ -19,13 +41,15 @@ struct Variant<1, W, NS, RR, MB> {
         (int)(sizeof(DBM_REAL) * NS * NARR * (W + 2 * Halo<DBM_REAL>::value) + 8 * NS);
     static void *single() { return (void *)step_kernel<DBM_REAL, W, NS>; }
     static void *batch() { return (void *)batch_step_kernel<DBM_REAL, W, NS>; }
-    static void run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
+    static cudaError_t run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
     {
         step_kernel<DBM_REAL, W, NS><<<g, kThreads, kSmem, s>>>(A);
+        return cudaGetLastError();
     }
-    static void run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
+    static cudaError_t run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
     {
         batch_step_kernel<DBM_REAL, W, NS><<<g, kThreads, kSmem, s>>>(B);
+        return cudaGetLastError();
     }
 };
 
@@ -35,13 +59,15 @@ struct VariantV2 {
     static constexpr int kSmem = smem_bytes_v2<DBM_REAL, W, NS>();
     static void *single() { return (void *)step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM>; }
     static void *batch() { return (void *)batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM>; }
-    static void run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
+    static cudaError_t run(const StepArgs<DBM_REAL> &A, int g, cudaStream_t s)
     {
         step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM><<<g, kThreads, kSmem, s>>>(A);
+        return cudaGetLastError();
     }
-    static void run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
+    static cudaError_t run_batch(const BatchArgs<DBM_REAL> &B, int g, cudaStream_t s)
     {
         batch_step_kernel_v2<DBM_REAL, W, NS, RR, MB, TM><<<g, kThreads, kSmem, s>>>(B);
+        return cudaGetLastError();
     }
 };
 
@@ -112,12 +138,11 @@ cudaError_t launch_step<DBM_REAL>(int variant, const StepArgs<DBM_REAL> &A, int 
 {
     switch (variant) {
 #define X(id, ver, W, NS, RR, MB) \
-    case id: Variant<ver, W, NS, RR, MB>::run(A, grid, s); break;
+    case id: return Variant<ver, W, NS, RR, MB>::run(A, grid, s);
         DBM_VARIANTS(X)
 #undef X
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <>
@@ -125,12 +150,11 @@ cudaError_t launch_batch_step<DBM_REAL>(int variant, const BatchArgs<DBM_REAL> &
 {
     switch (variant) {
 #define X(id, ver, W, NS, RR, MB) \
-    case id: Variant<ver, W, NS, RR, MB>::run_batch(B, grid, s); break;
+    case id: return Variant<ver, W, NS, RR, MB>::run_batch(B, grid, s);
         DBM_VARIANTS(X)
 #undef X
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <>

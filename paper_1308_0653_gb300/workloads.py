@@ -243,18 +243,26 @@ def arrivals(rate_hz: float, duration_s: float, seed: int = 0):
         n *= 2
 
 
-def serving_request(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
-                    smin: int = 1000, smax: int = 20000, align: int = 32) -> Workload:
-    """Request k of the serving stream: side N ~ logU[nmin, nmax] (stream 31,
-    multiple of `align`), steps ~ logU[smin, smax] (stream 32), explosion or
-    implosion with equal odds (stream 33), omega1 in {1, 2, 4} (stream 34)."""
+def serving_shape(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
+                  smin: int = 1000, smax: int = 20000, align: int = 32):
+    """(N, steps, explosion?, omega1) of request k of the serving stream, without
+    its fields: side N ~ logU[nmin, nmax] (stream 31, multiple of `align`),
+    steps ~ logU[smin, smax] (stream 32), explosion or implosion with equal
+    odds (stream 33), omega1 in {1, 2, 4} (stream 34)."""
     u = [uniform_at(seed, 31 + s, k) for s in range(4)]
     N = int(nmin * (nmax / nmin) ** u[0])
     N = max(align, (N // align) * align)
     steps = int(smin * (smax / smin) ** u[1])
     w1 = (1.0, 2.0, 4.0)[min(2, int(u[3] * 3))]
+    return N, steps, u[2] < 0.5, w1
+
+
+def serving_request(k: int, seed: int = 0, nmin: int = 128, nmax: int = 2048,
+                    smin: int = 1000, smax: int = 20000, align: int = 32) -> Workload:
+    """Request k of the serving stream (shape as serving_shape)."""
+    N, steps, is_explosion, w1 = serving_shape(k, seed, nmin, nmax, smin, smax, align)
     dt = 0.4 * min(1.0 / N, 0.05 * 2 * math.pi / N) / 12.5
-    if u[2] < 0.5:
+    if is_explosion:
         w = explosion(N, N, steps, seed=seed + k, omega1=w1, dt=dt)
     else:
         w = implosion(N, N, steps, seed=seed + k, omega1=w1, dt=dt)

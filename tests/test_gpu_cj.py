@@ -133,7 +133,10 @@ def test_fp32_run_tracks_the_fp64_run(runs):
     f and the rounding of every stored f counts."""
     a, b = runs["fp64"], runs["fp32"]
     n = W.planar_cj(nr=16, ntheta=1, sector=1).nsteps
-    assert abs(a["front"] - b["front"]) <= 4 * a["dr"]
     j = int(np.searchsorted(a["r"], a["front"] - 0.015))
+    drift = {k: float(abs(b["m"][k][j] / a["m"][k][j] - 1.0)) for k in ("rho", "T", "ur")}
+    print("CJ " + json.dumps(dict(case="fp32 vs fp64", front_cells=float(abs(a["front"] - b["front"]) / a["dr"]),
+                                  **{"plateau_" + k: v for k, v in drift.items()})))
+    assert abs(a["front"] - b["front"]) <= 4 * a["dr"]
     for k in ("rho", "T", "ur"):
         assert b["m"][k][j] == pytest.approx(a["m"][k][j], rel=n * 2.0 ** -24)

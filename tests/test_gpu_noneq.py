@@ -1,5 +1,7 @@
 """Non-equilibrium manifestations on the GPU (dbm_noneq, Sec. II.E) against
 the oracle's Delta*_m, and the paper's shock / rarefaction sign criterion."""
+import json
+
 import numpy as np
 import pytest
 
@@ -34,9 +36,12 @@ def test_noneq_matches_the_oracle(orc, precision, tol):
     for _ in range(w.nsteps):
         f, lam, _ = orc.step(p, f, lam)
     ref = orc.noneq(p, f)
+    errs = {}
     for c, name in enumerate(dbm.NONEQ):
         scale = max(np.abs(ref[c]).max(), 1e-3 * np.abs(ref[[0, 2, 9, 11]]).max())
-        err = np.abs(got[c] - ref[c]).max() / scale
+        errs[name] = float(np.abs(got[c] - ref[c]).max() / scale)
+    print("NONEQ", precision, json.dumps(errs))
+    for name, err in errs.items():
         assert err <= tol, (name, err)
 
 

@@ -49,6 +49,21 @@ def test_reactive_explosion_512_full(orc, precision):
     assert_close(out, ref, TOL[precision], f"explosion512 {precision}")
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_implosion_2048_over_1000_steps_matches_the_oracle(orc, precision):
+    """The 2048 x 2048 reactive implosion (the benchmark workload) for 1000
+    steps, both precisions against the oracle run once for the module
+    (1.4e11 site-velocity updates, about two minutes on 16 host cores): by
+    then the fastest particles (speed 12.5) have crossed 128 cells and the
+    driven shock about 15."""
+    w = W.implosion(2048, 2048, nsteps=1000, seed=0)
+    ref = run_oracle(orc, w)
+    assert ((ref["lam"] > 0.01) & (ref["lam"] < 0.99)).any()
+    out = run_gpu(w, precision)
+    assert out["launch"]["grid"] == 304
+    assert_close(out, ref, TOL[precision], f"implosion2048 1000 steps {precision}")
+
+
 @pytest.mark.parametrize("omega1", [1.0, 2.0, 4.0])
 def test_implosion_2048_in_bench_launch_shape(orc, omega1):
     """2048 x 2048 reactive implosion, FP32, 20 steps, for each of the rate

@@ -42,14 +42,53 @@ def test_sector_and_disc_match_the_oracle(orc, disc, nr, nth, precision):
     assert_close(out, ref, TOL[precision], f"sector nr={nr} nth={nth} disc={disc} {precision}")
 
 
+def _full_disc_workload(nr, nth, seed):
+    """Smooth random fields on a full 2 pi disc plus a uniform flow u_x = 0.3
+    straight through the centre, so the inner ghost (the cell across the
+    centre) differs from the cell itself in f and in lambda."""
+    w = W.random_smooth(nr, nth, seed=seed, amp=0.12, r_in=0.0, r_out=1.0, omega1=3.0,
+                        omega2=4.0, tau=5e-4, sector=0, r_bc_inner="centre")
+    _, th = W.grid(nr, nth, 0.0, 1.0)
+    w.fields["ur"] = np.ascontiguousarray(w.fields["ur"] + 0.3 * np.cos(th))
+    w.fields["uth"] = np.ascontiguousarray(w.fields["uth"] - 0.3 * np.sin(th))
+    dr = 1.0 / nr
+    w.params["dt"] = 0.35 * min(dr, dr / 2 * 2 * math.pi / nth) / 12.5
+    return w
+
+
+@pytest.mark.parametrize("nr,nth", [(40, 32), (70, 18)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_disc_matches_the_oracle(orc, nr, nth, precision):
+    """Full 2 pi disc with the centre rule (Sec. II.D): the ghost of the
+    innermost cell is the cell across the centre, row m + ntheta/2."""
+    w = _full_disc_workload(nr, nth, seed=nr + nth)
+    ref = run_oracle(orc, w, nsteps=80, r_bc_inner=1)
+    out = run_gpu(w, precision, nsteps=80)
+    assert_close(out, ref, TOL[precision], f"full disc nr={nr} nth={nth} {precision}")
+
+
+def test_full_disc_is_the_same_in_every_kernel_variant():
+    """Every step-kernel variant (row barrier, bulk copies, tensor maps, 4- and
+    6-deep rings) gives the same bits on a full disc."""
+    w = _full_disc_workload(40, 32, seed=5)
+    outs = []
+    for v in range(1, dbm.dbm_num_variants(dbm.DBM_FP32) + 1):
+        outs.append(run_gpu(w, "fp32", nsteps=40, variant=v))
+    for o in outs[1:]:
+        for k in ("rho", "ur", "uth", "T", "lam"):
+            assert np.array_equal(o[k], outs[0][k])
+
+
 def test_invalid_disc_configurations_are_rejected():
     p = dbm.dbm_params_default()
     p.r_bc_inner = dbm.DBM_BC_CENTRE
     p.r_in = 0.0
-    assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL   # centre needs a sector
-    p.sector = 1
     p.dt = 1e-7
-    assert dbm.dbm_check(p)[0] == dbm.DBM_OK
+    assert dbm.dbm_check(p)[0] == dbm.DBM_OK       # full disc, ntheta even
+    p.ntheta = 63
+    assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL   # full disc needs row m + ntheta/2
+    p.sector = 1
+    assert dbm.dbm_check(p)[0] == dbm.DBM_OK       # a sector needs no mirror row
     p.r_in = 0.01
     assert dbm.dbm_check(p)[0] == dbm.DBM_EINVAL   # centre needs r_in = 0
 
