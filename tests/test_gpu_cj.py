@@ -126,17 +126,20 @@ def test_peak_order_matches_the_paper(runs):
 
 
 def test_fp32_run_tracks_the_fp64_run(runs):
-    """Same wave in both precisions after 100 000 steps: fronts within four
-    cells, and the burnt plateau within n 2^-24 relative (n = steps), the
-    bound for one float rounding per step adding up with one sign.  The
-    run's dt / tau is 1.25e-3, so the per-step change of f is small against
-    f and the rounding of every stored f counts."""
+    """Same wave in both precisions after 100 000 steps (dt / tau = 1.25e-3,
+    so each step changes f by little against f, and the rounding of every
+    stored f counts).  Measured on a GB300: fronts 0.95 cell apart, plateau
+    rho 1.5e-4, T 3.0e-4, u_r 3.6e-4 apart.  The bounds are twice those:
+    a regression that doubled the FP32 drift fails.  (The bound of one float
+    rounding per step adding up with one sign, n 2^-24 = 6e-3, is 40 times
+    looser.)"""
     a, b = runs["fp64"], runs["fp32"]
     n = W.planar_cj(nr=16, ntheta=1, sector=1).nsteps
     j = int(np.searchsorted(a["r"], a["front"] - 0.015))
     drift = {k: float(abs(b["m"][k][j] / a["m"][k][j] - 1.0)) for k in ("rho", "T", "ur")}
     print("CJ " + json.dumps(dict(case="fp32 vs fp64", front_cells=float(abs(a["front"] - b["front"]) / a["dr"]),
                                   **{"plateau_" + k: v for k, v in drift.items()})))
-    assert abs(a["front"] - b["front"]) <= 4 * a["dr"]
+    assert abs(a["front"] - b["front"]) <= 2 * a["dr"]
+    bound = {"rho": 3e-4, "T": 6e-4, "ur": 7.5e-4}
     for k in ("rho", "T", "ur"):
-        assert b["m"][k][j] == pytest.approx(a["m"][k][j], rel=n * 2.0 ** -24)
+        assert drift[k] <= bound[k] < n * 2.0 ** -24, (k, drift[k])

@@ -20,11 +20,54 @@ def _cuda():
     torch.cuda.set_device(0)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-3)])
-def test_noneq_matches_the_oracle(orc, precision, tol):
-    """Same state (the GPU run exported after 60 steps is not used: the oracle
-    runs its own 60 steps from the same initial fields); Delta* components
-    relative to their largest magnitude."""
+def _errors(got, ref):
+    """Relative L-inf error of each Delta* component, scaled by its largest
+    oracle magnitude, floored at 1e-3 of the largest diagonal Delta*_2 and
+    Delta*_{4,2} (components odd in theta nearly vanish in a nearly
+    axisymmetric state)."""
+    errs = {}
+    for c, name in enumerate(dbm.NONEQ):
+        scale = max(np.abs(ref[c]).max(), 1e-3 * np.abs(ref[[0, 2, 9, 11]]).max())
+        errs[name] = float(np.abs(got[c] - ref[c]).max() / scale)
+    return errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noneq_of_the_same_state_matches_the_oracle(orc, precision):
+    """dbm_noneq evaluates Delta*_m in FP64 from the state, whatever the
+    state's precision: on the GPU's own state (exported, widened to double)
+    the oracle's Delta*_m agrees to FP64 round-off, in both precisions."""
+    w = W.explosion(128, 64, nsteps=60, seed=31, dt=2e-5)
+    sim = dbm.Simulation(dict(w.params, precision=precision))
+    sim.init_state(w.fields)
+    sim.step(w.nsteps)
+    got = sim.noneq()
+    f, _, _ = sim.export_state()
+    sim.close()
+    ref = orc.noneq(oracle_params(orc, w), np.ascontiguousarray(f, dtype=np.float64))
+    errs = _errors(got, ref)
+    print("NONEQ same state", precision, json.dumps(errs))
+    for name, err in errs.items():
+        assert err <= 1e-11, (name, err)
+
+
+# FP32 bounds, per group of components.  The kernel itself is exact to FP64
+# round-off on a given state (previous test), so the error is the FP32 state's
+# own difference from the FP64 run after 60 steps, about 1e-6 relative in the
+# moments, carried through Delta* = M*(f) - M*(f^eq): a difference of terms
+# of order rho T (2.3 at most here), so the error relative to a component's
+# scale is about 1e-6 rho T / scale.  Components even in theta have scales
+# 0.03 to 0.23 (Delta*_2rr = 0.032: 2.3 / 0.032 = 71, error ~7e-5; measured
+# at most 2.9e-5); those odd in theta nearly vanish in this nearly
+# axisymmetric state, scales 8e-4 to 8e-3 (Delta*_2rtheta = 1.7e-3: factor
+# 1300, error ~1.3e-3; measured at most 7.9e-4).  Bounds: 1e-4 and 1.6e-3.
+_EVEN = ("d2_rr", "d2_thth", "d3_rrr", "d3_rthth", "d31_r", "d42_rr", "d42_thth")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noneq_matches_the_oracle(orc, precision):
+    """The GPU run and the oracle run from the same initial fields (60 steps
+    each); Delta* components relative to their largest magnitude."""
     w = W.explosion(128, 64, nsteps=60, seed=31, dt=2e-5)
     sim = dbm.Simulation(dict(w.params, precision=precision))
     sim.init_state(w.fields)
@@ -36,12 +79,10 @@ def test_noneq_matches_the_oracle(orc, precision, tol):
     for _ in range(w.nsteps):
         f, lam, _ = orc.step(p, f, lam)
     ref = orc.noneq(p, f)
-    errs = {}
-    for c, name in enumerate(dbm.NONEQ):
-        scale = max(np.abs(ref[c]).max(), 1e-3 * np.abs(ref[[0, 2, 9, 11]]).max())
-        errs[name] = float(np.abs(got[c] - ref[c]).max() / scale)
+    errs = _errors(got, ref)
     print("NONEQ", precision, json.dumps(errs))
     for name, err in errs.items():
+        tol = 1e-10 if precision == "fp64" else (1e-4 if name in _EVEN else 1.6e-3)
         assert err <= tol, (name, err)
 
 
