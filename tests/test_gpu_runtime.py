@@ -167,3 +167,63 @@ def test_bounded_wait_runs_out_reports_and_leaves_the_context_usable():
     out.close()
     with pytest.raises(Exception):
         dbm.dbm_selftest_wait(st.data_ptr(), False, 0)          # invalid limit
+
+
+def test_device_init_check_is_reported_by_status_and_cleared_by_a_good_init():
+    """dbm_init_state_device checks the fields on the GPU without waiting: a
+    bad value is reported by the next dbm_status as DBM_EINVAL, and a later
+    init with valid fields clears it."""
+    import torch
+    w = W.explosion(64, 16, nsteps=0, seed=10)
+    sim = dbm.Simulation(dict(w.params, precision="fp32"))
+    fields = np.stack([w.fields[k] for k in ("rho", "ur", "uth", "T", "lam")])
+    bad = fields.copy()
+    bad[0, 3, 5] = 0.0                                   # rho = 0
+    d_bad = torch.from_numpy(bad).cuda()
+    dbm.dbm_init_state_device(sim.h, d_bad.data_ptr())
+    assert dbm.dbm_status(sim.h) == dbm.DBM_EINVAL
+    bad[0, 3, 5] = np.nan
+    d_bad.copy_(torch.from_numpy(bad))
+    dbm.dbm_init_state_device(sim.h, d_bad.data_ptr())
+    assert dbm.dbm_status(sim.h) == dbm.DBM_EINVAL
+    d_good = torch.from_numpy(fields).cuda()
+    dbm.dbm_init_state_device(sim.h, d_good.data_ptr())
+    assert dbm.dbm_status(sim.h) == dbm.DBM_OK
+    sim.close()
+
+
+def test_destroy_waits_for_the_handles_queued_steps():
+    """dbm_destroy returns only after the GPU has finished the steps queued
+    on the handle's buffers: the stream they were queued on is idle then."""
+    import torch
+    w = W.implosion(1024, 1024, nsteps=0)
+    p = dbm.params_from(dict(w.params, precision="fp32"))
+    need = dbm.dbm_state_bytes(p)
+    buf = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    h = dbm.dbm_create(p, ptr, need)
+    s = torch.cuda.Stream()
+    dbm.dbm_init_state(h, *[w.fields[k] for k in ("rho", "ur", "uth", "T", "lam")], stream=s)
+    dbm.dbm_step(h, 400, s)                              # about 20 ms of work
+    assert not s.query()                                 # still running
+    dbm.dbm_destroy(h)
+    assert s.query()                                     # finished before destroy returned
+
+
+def test_batches_share_the_constant_table_and_give_entries_back():
+    """Every live batch holds max_slots entries of the per-precision constant
+    table (256 FP32 entries per device): a batch that does not fit is refused
+    with DBM_ENOMEM, and a destroyed batch's entries can be taken again."""
+    import gc
+    gc.collect()                                         # batches of earlier tests
+    a = dbm.Batch(200, 1024, precision="fp32")
+    with pytest.raises(dbm.DbmError) as e:
+        dbm.Batch(100, 1024, precision="fp32")
+    assert e.value.status == dbm.DBM_ENOMEM
+    b = dbm.Batch(56, 1024, precision="fp32")            # 200 + 56 = 256: fits
+    a.close()
+    c = dbm.Batch(150, 1024, precision="fp32")
+    c.close()
+    b.close()
+    d = dbm.Batch(256, 1024, precision="fp32")
+    d.close()
