@@ -159,6 +159,8 @@ struct dbm_s {
     bool tmap_ok;             // tensor maps encoded (tensor-TMA variants usable)
     cudaEvent_t done;         // recorded after the last work that touches the buffers
     int host_word[2];         // host side of small device-to-host status copies
+    cudaStream_t aux;         // second stream of the chunked host-array calls
+    cudaEvent_t chunk_ev[4], join_ev;
 };
 
 namespace {
@@ -587,6 +589,10 @@ static void free_handle(dbm_t *h)
 {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->done) cudaEventDestroy(h->done);
+    for (cudaEvent_t ev : h->chunk_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->aux) cudaStreamDestroy(h->aux);
     delete h;
 }
 
@@ -611,9 +617,13 @@ int dbm_create(const dbm_params *p, void *dev_buf, size_t dev_bytes, dbm_t **out
     h->plane = (long long)h->ld * p->ntheta;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming);
+    for (cudaEvent_t &ev : h->chunk_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-        delete h;
-        return cuda_fail(e, "dbm_create: device query");
+        free_handle(h);
+        return cuda_fail(e, "dbm_create: device query, events and streams");
     }
     const int v0 = pick_variant(*p);
     rc = configure_launch(h, v0);
@@ -658,7 +668,7 @@ int dbm_destroy(dbm_t *h)
 }  // extern "C"
 
 template <typename real>
-static cudaError_t launch_init_as(dbm_t *h, const double *d_fields, cudaStream_t s)
+static cudaError_t launch_init_as(dbm_t *h, const double *d_fields, cudaStream_t s, int m0, int m1)
 {
     double Fc[4][4];
     weight_coeffs(h->p.v, Fc);
@@ -673,6 +683,8 @@ static cudaError_t launch_init_as(dbm_t *h, const double *d_fields, cudaStream_t
     A.nr = h->p.nr;
     A.ntheta = h->p.ntheta;
     A.ld = h->ld;
+    A.m0 = m0;
+    A.m1 = m1;
     for (int k = 0; k < 4; ++k) {
         A.v[k] = (real)h->p.v[k];
         for (int c = 0; c < 4; ++c) A.Fc[k][c] = (real)Fc[k][c];
@@ -682,17 +694,33 @@ static cudaError_t launch_init_as(dbm_t *h, const double *d_fields, cudaStream_t
 
 extern "C" {
 
-// f = f^eq of the device fields into buffer 0; the kernel checks every value
-// and sets the handle's bad-input word (cleared here first) on a bad one.
+// f = f^eq of the device fields into buffer 0 for theta rows [m0, m1); the
+// kernel checks every value and sets the handle's bad-input word.
+static int launch_init_rows(dbm_t *h, const double *d_fields, cudaStream_t s, int m0, int m1)
+{
+    const cudaError_t e = h->p.precision == DBM_FP64 ? launch_init_as<double>(h, d_fields, s, m0, m1)
+                                                     : launch_init_as<float>(h, d_fields, s, m0, m1);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
+    return DBM_OK;
+}
+
 static int launch_init_from(dbm_t *h, const double *d_fields, cudaStream_t s)
 {
     CK(cudaMemsetAsync(bad_input_word(h), 0, sizeof(int), s));
-    const cudaError_t e = h->p.precision == DBM_FP64 ? launch_init_as<double>(h, d_fields, s)
-                                                     : launch_init_as<float>(h, d_fields, s);
-    if (e != cudaSuccess) return cuda_fail(e, "init kernel launch");
+    const int rc = launch_init_rows(h, d_fields, s, 0, h->p.ntheta);
+    if (rc != DBM_OK) return rc;
     h->cur = 0;
     h->steps = 0;
     return DBM_OK;
+}
+
+// Theta-row chunks of the host-array calls: their copies over the host link
+// (about 200 GB/s) overlap the init or moments kernel of the neighbouring
+// chunk, which runs on the handle's second stream.  Small grids are one chunk.
+static int host_chunks(const dbm_t *h)
+{
+    const size_t bytes = (size_t)5 * h->p.nr * h->p.ntheta * sizeof(double);
+    return (bytes >= ((size_t)32 << 20) && h->p.ntheta >= 16) ? 4 : 1;
 }
 
 int dbm_init_state(dbm_t *h, const double *rho, const double *ur, const double *uth,
@@ -700,17 +728,40 @@ int dbm_init_state(dbm_t *h, const double *rho, const double *ur, const double *
 {
     if (!h || !rho || !ur || !uth || !T || !lam) return DBM_EINVAL;
     const size_t N = (size_t)h->p.nr * h->p.ntheta;
+    const int nr = h->p.nr, nth = h->p.ntheta;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // Stage the fields in the second f buffer (free before the first step);
     // the init kernel validates them on the GPU, and one synchronisation at
     // the end covers the copies (the host arrays may be reused on return)
-    // and the validation result.
+    // and the validation result.  Chunk c's copies go on `stream`, its init
+    // kernel on the second stream once they have landed, while chunk c + 1
+    // is copied.
     double *stage = reinterpret_cast<double *>(h->buf + h->L.f[1]);
     const double *src[5] = {rho, ur, uth, T, lam};
-    for (int c = 0; c < 5; ++c)
-        CK(cudaMemcpyAsync(stage + c * N, src[c], N * sizeof(double), cudaMemcpyHostToDevice, s));
-    int rc = launch_init_from(h, stage, s);
-    if (rc != DBM_OK) return rc;
+    const int C = host_chunks(h);
+    const int R = (nth + C - 1) / C;
+    CK(cudaMemsetAsync(bad_input_word(h), 0, sizeof(int), s));
+    for (int c = 0; c < C; ++c) {
+        const int m0 = c * R, m1 = std::min(nth, m0 + R);
+        if (m0 >= m1) break;
+        const size_t off = (size_t)m0 * nr, cnt = (size_t)(m1 - m0) * nr;
+        for (int f = 0; f < 5; ++f)
+            CK(cudaMemcpyAsync(stage + f * N + off, src[f] + off, cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+        cudaStream_t ks = s;
+        if (C > 1) {
+            CK(cudaEventRecord(h->chunk_ev[c], s));
+            CK(cudaStreamWaitEvent(h->aux, h->chunk_ev[c], 0));
+            ks = h->aux;
+        }
+        const int rc = launch_init_rows(h, stage, ks, m0, m1);
+        if (rc != DBM_OK) return rc;
+    }
+    if (C > 1) {
+        CK(cudaEventRecord(h->join_ev, h->aux));
+        CK(cudaStreamWaitEvent(s, h->join_ev, 0));
+    }
+    h->cur = 0;
+    h->steps = 0;
     CK(cudaMemcpyAsync(&h->host_word[0], bad_input_word(h), sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     note_work(h, s);
@@ -756,7 +807,8 @@ int dbm_step(dbm_t *h, int64_t nsteps, void *stream)
 }  // extern "C"
 
 template <typename real>
-static cudaError_t launch_moments_as(dbm_t *h, double *d_out, double *partials, int grid, cudaStream_t s)
+static cudaError_t launch_moments_as(dbm_t *h, double *d_out, double *partials, int grid, cudaStream_t s,
+                                     int m0, int m1)
 {
     const dbm_params &p = h->p;
     MomArgs<real> A;
@@ -780,23 +832,42 @@ static cudaError_t launch_moments_as(dbm_t *h, double *d_out, double *partials, 
         A.vr[k] = (real)p.v[k];
         A.v2r[k] = (real)(p.v[k] * p.v[k]);
     }
+    A.m0 = m0;
+    A.m1 = m1;
     return launch_moments<real>(A, grid, s);
 }
 
 extern "C" {
 
-static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
+// Moments of theta rows [m0, m1) into d_out, their per-block partial sums at
+// partial slot *slot0 onwards (advanced past them), at most max_blocks blocks.
+static int launch_moments_rows(dbm_t *h, double *d_out, cudaStream_t s, int m0, int m1, int max_blocks,
+                               int *slot0)
 {
-    const dbm_params &p = h->p;
-    const long long N = (long long)p.nr * p.ntheta;
-    int grid = (int)std::min<long long>((N + 255) / 256, MOMENT_BLOCKS);
-    double *partials = reinterpret_cast<double *>(h->buf + h->L.partials);
-    cudaError_t e = p.precision == DBM_FP64 ? launch_moments_as<double>(h, d_out, partials, grid, s)
-                                            : launch_moments_as<float>(h, d_out, partials, grid, s);
+    const long long n = (long long)h->p.nr * (m1 - m0);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, max_blocks));
+    double *partials = reinterpret_cast<double *>(h->buf + h->L.partials) + (size_t)*slot0 * 4;
+    const cudaError_t e = h->p.precision == DBM_FP64 ? launch_moments_as<double>(h, d_out, partials, grid, s, m0, m1)
+                                                     : launch_moments_as<float>(h, d_out, partials, grid, s, m0, m1);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
-    e = launch_totals(partials, grid, reinterpret_cast<double *>(h->buf + h->L.totals), s);
+    *slot0 += grid;
+    return DBM_OK;
+}
+
+static int launch_totals_of(dbm_t *h, int nblocks, cudaStream_t s)
+{
+    const cudaError_t e = launch_totals(reinterpret_cast<double *>(h->buf + h->L.partials), nblocks,
+                                        reinterpret_cast<double *>(h->buf + h->L.totals), s);
     if (e != cudaSuccess) return cuda_fail(e, "totals kernel launch");
     return DBM_OK;
+}
+
+static int launch_moments_into(dbm_t *h, double *d_out, cudaStream_t s)
+{
+    int nblocks = 0;
+    int rc = launch_moments_rows(h, d_out, s, 0, h->p.ntheta, MOMENT_BLOCKS, &nblocks);
+    if (rc != DBM_OK) return rc;
+    return launch_totals_of(h, nblocks, s);
 }
 
 static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
@@ -816,6 +887,8 @@ static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.ld = h->ld;
         A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
+        A.m0 = 0;
+        A.m1 = p.ntheta;
         e = launch_noneq<double>(A, grid, s);
     } else {
         MomArgs<float> A;
@@ -828,6 +901,8 @@ static int launch_noneq_into(dbm_t *h, double *d_out, cudaStream_t s)
         A.ld = h->ld;
         A.th_over_pi = theta_span(p) / PI / p.ntheta;
         std::memcpy(A.v, p.v, sizeof(A.v));
+        A.m0 = 0;
+        A.m1 = p.ntheta;
         e = launch_noneq<float>(A, grid, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "noneq kernel launch");
@@ -872,16 +947,39 @@ int dbm_moments(dbm_t *h, double *rho, double *ur, double *uth, double *T, doubl
     if (!h) return DBM_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t N = (size_t)h->p.nr * h->p.ntheta;
+    const int nr = h->p.nr, nth = h->p.ntheta;
     double *stage = reinterpret_cast<double *>(h->buf + h->L.f[1 - h->cur]);
-    int rc = launch_moments_into(h, stage, s);
-    if (rc != DBM_OK) return rc;
     double *dst[5] = {rho, ur, uth, T, lam};
-    for (int c = 0; c < 5; ++c)
-        if (dst[c])
-            CK(cudaMemcpyAsync(dst[c], stage + c * N, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // Chunk c's moments kernel on `stream`; its copies to the host arrays on
+    // the second stream once it is done, while chunk c + 1 is computed.
+    const int C = host_chunks(h);
+    const int R = (nth + C - 1) / C;
+    int nblocks = 0;
+    for (int c = 0; c < C; ++c) {
+        const int m0 = c * R, m1 = std::min(nth, m0 + R);
+        if (m0 >= m1) break;
+        int rc = launch_moments_rows(h, stage, s, m0, m1, MOMENT_BLOCKS / C, &nblocks);
+        if (rc != DBM_OK) return rc;
+        cudaStream_t cs = s;
+        if (C > 1) {
+            CK(cudaEventRecord(h->chunk_ev[c], s));
+            CK(cudaStreamWaitEvent(h->aux, h->chunk_ev[c], 0));
+            cs = h->aux;
+        }
+        const size_t off = (size_t)m0 * nr, cnt = (size_t)(m1 - m0) * nr;
+        for (int f = 0; f < 5; ++f)
+            if (dst[f])
+                CK(cudaMemcpyAsync(dst[f] + off, stage + f * N + off, cnt * sizeof(double), cudaMemcpyDeviceToHost, cs));
+    }
+    int rc = launch_totals_of(h, nblocks, s);
+    if (rc != DBM_OK) return rc;
     if (totals)
         CK(cudaMemcpyAsync(totals, h->buf + h->L.totals, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(h->host_word, h->buf + h->L.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (C > 1) {
+        CK(cudaEventRecord(h->join_ev, h->aux));
+        CK(cudaStreamWaitEvent(s, h->join_ev, 0));
+    }
     CK(cudaStreamSynchronize(s));
     const int status = h->host_word[0];
     if (status & ST_WAIT_TIMEOUT) return DBM_ETIMEOUT;

@@ -1239,6 +1239,7 @@ struct InitArgs {
     int *bad;
     long long plane;
     int nr, ntheta, ld;
+    int m0, m1;          // theta rows [m0, m1) of this launch
     real v[4];
     real Fc[4][4];
 };
@@ -1251,8 +1252,8 @@ __global__ void __launch_bounds__(256) init_kernel(const InitArgs<real> A)
     const real one = real(1), half = real(0.5);
     const long long N = (long long)A.nr * A.ntheta;
     bool bad = false;
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
+    for (long long s = (long long)A.m0 * A.nr + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         s < (long long)A.m1 * A.nr; s += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
         const double rho_d = A.fields[s], ur_d = A.fields[N + s], uth_d = A.fields[2 * N + s];
         const double T_d = A.fields[3 * N + s], lam_d = A.fields[4 * N + s];
@@ -1324,6 +1325,7 @@ struct MomArgs {
     double th_over_pi;  // theta_m / pi per row
     double v[4];
     real vr[4], v2r[4];  // ring speeds and squares in real (FP32 moments)
+    int m0, m1;          // theta rows [m0, m1) of this launch
 };
 
 template <typename real>
@@ -1334,8 +1336,8 @@ __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
     bool bad = false;
     if constexpr (sizeof(real) == 4) {
         using O = Op<float>;
-        for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-             s += (long long)gridDim.x * blockDim.x) {
+        for (long long s = (long long)A.m0 * A.nr + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+             s < (long long)A.m1 * A.nr; s += (long long)gridDim.x * blockDim.x) {
             const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
             const float *fp = A.f + (long long)m * A.ld + j;
             float fv[NV];
@@ -1373,8 +1375,8 @@ __global__ void __launch_bounds__(256) moments_kernel(const MomArgs<real> A)
     } else {
         double cx[8], cy[8];
         cart_dirs(cx, cy);
-        for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-             s += (long long)gridDim.x * blockDim.x) {
+        for (long long s = (long long)A.m0 * A.nr + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+             s < (long long)A.m1 * A.nr; s += (long long)gridDim.x * blockDim.x) {
             const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
             const real *fp = A.f + (long long)m * A.ld + j;
             double fv[NV];
@@ -1447,8 +1449,8 @@ __global__ void __launch_bounds__(256) noneq_kernel(const MomArgs<real> A)
     const long long N = (long long)A.nr * A.ntheta;
     double cx[8], cy[8];
     cart_dirs(cx, cy);
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
+    for (long long s = (long long)A.m0 * A.nr + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+         s < (long long)A.m1 * A.nr; s += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(s / A.nr), j = (int)(s - (long long)m * A.nr);
         const real *fp = A.f + (long long)m * A.ld + j;
         double fv[NV];

@@ -160,8 +160,9 @@ cudaError_t launch_batch_step<DBM_REAL>(int variant, const BatchArgs<DBM_REAL> &
 template <>
 cudaError_t launch_init<DBM_REAL>(const InitArgs<DBM_REAL> &A, cudaStream_t s)
 {
-    const long long n = (long long)A.nr * A.ntheta;
+    const long long n = (long long)A.nr * (A.m1 - A.m0);
     const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (n <= 0) return cudaSuccess;
     init_kernel<DBM_REAL><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
