@@ -273,3 +273,21 @@ def test_implosion_2048_full_length_fp32_tracks_fp64():
     a = run_gpu(w, "fp32")
     b = run_gpu(w, "fp64")
     assert_close(a, b, TOL["fp32"], "implosion2048 20000 steps fp32 vs fp64")
+
+
+def test_large_grid_uniform_state_stays_uniform():
+    """16384 x 8192 sites (36.5 GB of FP32 state): the offsets of the
+    velocity planes pass 2^31 elements, the TMA row coordinates reach 8191,
+    and the launch holds 2432 work items of 432 rows (8 per CTA).  A uniform
+    moving state is a fixed point of the update, so after 4 steps every site
+    still holds it (FP32)."""
+    import torch
+    nr, nth = 16384, 8192
+    w = W.uniform_state(nr, nth, 1.3, 0.3, -0.2, 1.2, 0.4, r_in=1.0, r_out=2.0, dt=2e-6)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60e9:
+        pytest.skip("needs about 40 GB of free device memory")
+    out = run_gpu(w, "fp32", nsteps=4)
+    assert out["launch"]["items"] == 2432 and out["launch"]["rows_per_item"] == 432
+    for k in FIELDS:
+        np.testing.assert_allclose(out[k], w.fields[k], atol=2e-6 * max(1.0, np.abs(w.fields[k]).max()))
