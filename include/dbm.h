@@ -84,7 +84,7 @@ typedef struct dbm_params {
     int32_t nr, ntheta;        /* grid size, both >= 1                            */
     int32_t precision;         /* DBM_FP32 or DBM_FP64                            */
     int32_t reaction_energy;   /* DBM_R_EXPLICIT (default) or DBM_R_CONSISTENT     */
-    int32_t r_bc_inner;        /* DBM_BC_OUTFLOW                                  */
+    int32_t r_bc_inner;        /* DBM_BC_OUTFLOW or DBM_BC_CENTRE (r_in = 0)      */
     int32_t r_bc_outer;        /* DBM_BC_OUTFLOW                                  */
     int32_t rows_per_item;     /* theta rows per CTA work item; 0 = automatic     */
     int32_t variant;           /* step-kernel variant 1..dbm_num_variants();      */
@@ -376,8 +376,15 @@ int dbm_batch_plan(int32_t nslots, const int32_t *nr, const int32_t *ntheta, con
 /* Create a batch on caller device memory (256-byte aligned, >=
  * dbm_batch_bytes).  rows_per_item: theta rows per work item (0 = 16; -1 =
  * scaled to each simulation: 16 up to 512 theta rows, 32 up to 1024, else 64).
- * Allocates a pinned host staging buffer for the tables.  Synchronous.
- * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
+ * Allocates a pinned host staging buffer for the tables and takes max_slots
+ * entries of the device's batch constant table (per-slot constants read by
+ * the batched kernel from constant memory; DBM_BATCH_CONST_FP32 /
+ * DBM_BATCH_CONST_FP64 entries per device and precision, shared by all live
+ * batches of the process, given back by dbm_batch_destroy).  Synchronous.
+ * Errors: DBM_EINVAL, DBM_ENOMEM (buffer too small, or fewer than max_slots
+ * free table entries), DBM_ECUDA. */
+#define DBM_BATCH_CONST_FP32 256
+#define DBM_BATCH_CONST_FP64 128
 int dbm_batch_create(int max_slots, int64_t max_items, int precision, int rows_per_item,
                      void *dev_buf, size_t dev_bytes, dbm_batch_t **out);
 
@@ -493,7 +500,8 @@ size_t dbm_server_min_bytes(const dbm_server_config *cfg);
 
 /* Start a server on caller device memory (256-byte aligned), on the current
  * device.  The caller keeps ownership of dev_pool until dbm_server_destroy.
- * Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
+ * Its batch takes max_slots entries of the batch constant table (see
+ * dbm_batch_create).  Errors: DBM_EINVAL, DBM_ENOMEM, DBM_ECUDA. */
 int dbm_server_create(const dbm_server_config *cfg, void *dev_pool, size_t pool_bytes,
                       dbm_server_t **out);
 

@@ -5,12 +5,13 @@
 //   3  v2  128  4  yes  3   as 2 with a 4-deep ring (74 KB) and <= 136 registers
 //   4  v3  128  6  no   2   as 2, rows loaded by tensor-map TMA (3 copies per row)
 //   5  v3  128  4  yes  3   as 3, rows loaded by tensor-map TMA
+#include "dbm.h"
 #define DBM_REAL float
 #define DBM_VARIANTS(X) X(1, 1, 128, 6, false, 2) X(2, 2, 128, 6, false, 2) X(3, 2, 128, 4, true, 3) \
     X(4, 3, 128, 6, false, 2) X(5, 3, 128, 4, true, 3)
 #define DBM_DEFAULT_VARIANT 4
 #define DBM_FALLBACK_VARIANT 2
-#define DBM_BATCH_CONST_SLOTS 256  // batch constant table entries (160 B each)
+#define DBM_BATCH_CONST_SLOTS DBM_BATCH_CONST_FP32  // batch constant table entries (160 B each)
 #include "dbm_launch_impl.cuh"
 
 namespace dbm {
