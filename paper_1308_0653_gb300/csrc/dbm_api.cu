@@ -122,19 +122,30 @@ double theta_span(const dbm_params &p) { return p.sector ? PI / 4.0 : 2.0 * PI; 
 
 void row_angles(const dbm_params &p, int m, double c[8], double s[8])
 {
-    for (int i = 0; i < 8; ++i) {
-        double ang;
-        if (p.sector) {
-            ang = i * PI / 4.0 - m * (PI / 4.0 / p.ntheta);
-        } else if (p.ntheta % 8 == 0) {
+    // Directions i and i + 4 are opposite: their entries are exact negatives
+    // of each other (the step shares |C_r|, |C_theta| between them).  With
+    // 8 | ntheta on a full grid the entry depends on q = (i ntheta/8 - m) mod
+    // ntheta alone (8-fold rotation equivariance, bit for bit), and the half
+    // turn q + ntheta/2 is the negation of q.
+    if (!p.sector && p.ntheta % 8 == 0) {
+        const long long half = p.ntheta / 2;
+        for (int i = 0; i < 8; ++i) {
             long long q = ((long long)i * (p.ntheta / 8) - m) % p.ntheta;
             if (q < 0) q += p.ntheta;
-            ang = 2.0 * PI * (double)q / p.ntheta;
-        } else {
-            ang = i * PI / 4.0 - m * (2.0 * PI / p.ntheta);
+            const double sign = q < half ? 1.0 : -1.0;
+            const double ang = 2.0 * PI * (double)(q < half ? q : q - half) / p.ntheta;
+            c[i] = sign * std::cos(ang);
+            s[i] = sign * std::sin(ang);
         }
+        return;
+    }
+    for (int i = 0; i < 4; ++i) {
+        const double ang = p.sector ? i * PI / 4.0 - m * (PI / 4.0 / p.ntheta)
+                                    : i * PI / 4.0 - m * (2.0 * PI / p.ntheta);
         c[i] = std::cos(ang);
         s[i] = std::sin(ang);
+        c[i + 4] = -c[i];
+        s[i + 4] = -s[i];
     }
 }
 

@@ -504,9 +504,17 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const StepC
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             // as geom(i, ...), written out: the compiler schedules this form better
-            ar[i] = O::mul(fabs(cs[i]), C.cr_scale);
-            at[i] = O::mul(O::mul(fabs(sn8[i]), C.ct_scale), inv_r);
-            sa[i] = O::add(ar[i], at[i]);
+            if (sizeof(real) == 8 && i >= 4) {
+                // FP64: the trig table holds direction i + 4 as the exact
+                // negation of direction i, so the magnitudes are the same bits
+                ar[i] = ar[i - 4];
+                at[i] = at[i - 4];
+                sa[i] = sa[i - 4];
+            } else {
+                ar[i] = O::mul(fabs(cs[i]), C.cr_scale);
+                at[i] = O::mul(O::mul(fabs(sn8[i]), C.ct_scale), inv_r);
+                sa[i] = O::add(ar[i], at[i]);
+            }
             int o = cs[i] >= real(0) ? -1 : 1;  // C_r >= 0: backward difference
             if (j == 0 && o < 0) {
                 o = C.centre == 1 ? (((i + 4) & 7) - i) * WP : (C.centre == 2 ? -1 : 0);
@@ -550,15 +558,27 @@ __device__ __forceinline__ void site_update(const StepArgs<real> &A, const StepC
             if constexpr (sizeof(real) == 8) {
                 // FP64 is bound by its arithmetic: opposite directions i and
                 // i+4 have xi and -xi, so the polynomial splits into an even
-                // part E and an odd part O evaluated once, poly(+-xi) = E +- O
+                // part E and an odd part O evaluated once, poly(+-xi) = E +- O;
+                // they also share |C_r| + |C_theta|, so the weight of the
+                // site's own f, E - v_k (|C_r| + |C_theta|), is taken once
+                auto update_pair_one = [&](int i, real xi, real poly, real keep) {
+                    const int q = 1 + 8 * k + i;
+                    real t = O::mul(poly, O::fma(-gamma, xi, beta));
+                    const real fq = REREAD ? sc[q * WP + col] : f[q];
+                    t = O::fma(keep, fq, t);
+                    const real adv = O::fma(ar[i], sc[q * WP + rn[i]], O::mul(at[i], sc[q * WP + tn[i]]));
+                    t = O::fma(vk, adv, t);
+                    out[(long long)q * A.plane] = t;
+                };
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const real xi = O::mul(vk, w[i]);
                     const real x2 = O::mul(xi, xi);
                     const real Ev = O::fma(x2, O::fma(x2, real(1.0 / 24.0), A2), A0);
                     const real Od = O::mul(xi, O::fma(x2, real(1.0 / 6.0), A1));
-                    update_one(i, xi, O::add(Ev, Od));
-                    update_one(i + 4, -xi, O::sub(Ev, Od));
+                    const real keep = O::fma(-vk, sa[i], C.decay);
+                    update_pair_one(i, xi, O::add(Ev, Od), keep);
+                    update_pair_one(i + 4, -xi, O::sub(Ev, Od), keep);
                 }
             } else {
 #pragma unroll
