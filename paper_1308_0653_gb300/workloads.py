@@ -139,7 +139,9 @@ def implosion(nr: int = 2048, ntheta: int = 2048, nsteps: int = 20000, seed: int
     phase = 2.0 * math.pi * uniform(seed, 3, modes.size)
 
     def outside(r, th):
-        pert = (amp[None, None, :] * np.cos(modes[None, None, :] * th[..., None]
+        # r_s depends on theta alone: one value per row, broadcast over the row's sites
+        t = th[:, :1]
+        pert = (amp[None, None, :] * np.cos(modes[None, None, :] * t[..., None]
                                             + phase[None, None, :])).sum(-1) / amp.sum()
         return r > r_shock * (1.0 + 0.005 * pert)
 
