@@ -53,6 +53,23 @@ def test_implosion_recipe():
     assert max(front) - min(front) >= r[0, 1] - r[0, 0]
 
 
+@pytest.mark.parametrize("nr,ntheta,seed", [(256, 256, 0), (200, 96, 3), (33, 7, 5)])
+def test_implosion_front_follows_its_formula_at_every_site(nr, ntheta, seed):
+    """The shocked region is exactly r > r_s(theta) with r_s = 0.9 [1 + 0.005
+    sum_q a_q cos(q theta + phi_q) / sum a_q], q = 4..16, a_q from stream 2 and
+    phi_q / 2 pi from stream 3, evaluated here site by site."""
+    w = W.implosion(nr, ntheta, nsteps=0, seed=seed)
+    r, th = W.grid(nr, ntheta, w.params["r_in"], w.params["r_out"])
+    a = W.uniform(seed, 2, 13)
+    phi = 2.0 * math.pi * W.uniform(seed, 3, 13)
+    q = np.arange(4, 17)
+    rs = np.empty((ntheta, nr))
+    for m in range(ntheta):
+        for j in range(nr):
+            rs[m, j] = 0.9 * (1.0 + 0.005 * (a * np.cos(q * th[m, j] + phi)).sum() / a.sum())
+    assert np.array_equal(w.fields["lam"] == 1.0, r > rs)
+
+
 def test_batch_recipe():
     ws = W.batch(64, seed=0, nsteps=5)
     sides = [w.params["nr"] for w in ws]
